@@ -1,0 +1,144 @@
+"""Seeded synthetic inputs (diffusion coefficient fields, right-hand sides,
+boundary flags) for the five workloads.  This module holds none of the
+method's arithmetic: it only draws numbers.  It is the one module that both
+the CUDA path's tests/benchmark and the CPU oracle's tests take inputs from.
+
+Index order is x fastest: a = x + nx*(y + ny*z).  Draw order: kappa
+parameters first, then right-hand sides.  Every generator takes an explicit
+seed and uses numpy's default_rng(seed).
+
+Workloads (unit cube, Dirichlet u=0 on the z=0 and z=1 faces, Neumann on the
+x and y faces, unless stated):
+  blocks32     32^3, kappa = 10^e on a 4x4x4 block partition, e uniform integer
+               in [-3, 3]; b ~ N(0,1)
+  layered128   128^3, 16 z-layers alternating kappa 1 and 1e6, eight 16^3
+               inclusions of kappa 1e-3; b = h^3 (f = 1 scaled by cell volume)
+  grf350       350^3, kappa = 10^(3 g), g a Gaussian random field with
+               correlation length 0.1, normalised, clipped to [-1, 1]; b ~ N(0,1)
+  batched      64 instances, each nx,ny,nz uniform in [48, 160], kappa = 10^e on
+               an 8x8x8 block partition, 4 right-hand sides N(0,1) each
+  grf_train    64^3 GRF instances with contrast 10^4 (kappa = 10^(2 g))
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# x-, x+, y-, y+, z-, z+ ; 0 = Dirichlet, 1 = Neumann
+BC_Z_DIRICHLET = (1, 1, 1, 1, 0, 0)
+BC_ALL_DIRICHLET = (0, 0, 0, 0, 0, 0)
+
+
+def kappa_blocks(grid, nblocks, seed, emin=-3, emax=3, rng=None):
+    """kappa = 10^e, e an integer uniform in [emin, emax] per block of an
+    nblocks^3 partition; a cell with coordinate c along an axis of n cells is
+    in block floor(nblocks * c / n)."""
+    nx, ny, nz = grid
+    rng = np.random.default_rng(seed) if rng is None else rng
+    e = rng.integers(emin, emax + 1, size=(nblocks, nblocks, nblocks))  # [bz, by, bx]
+    bx = (nblocks * np.arange(nx)) // nx
+    by = (nblocks * np.arange(ny)) // ny
+    bz = (nblocks * np.arange(nz)) // nz
+    ee = e[bz[:, None, None], by[None, :, None], bx[None, None, :]]
+    return np.power(10.0, ee).reshape(-1)
+
+
+def kappa_layered(n, seed, layers=16, hi=1e6, lo=1.0, incl=8, incl_size=16, incl_val=1e-3, rng=None):
+    """z-layers of n/layers cells alternating lo (even layer, from z=0) and hi,
+    then `incl` cubes of incl_size^3 cells with kappa = incl_val at corners drawn
+    uniformly in [0, n - incl_size] (later ones overwrite earlier ones)."""
+    rng = np.random.default_rng(seed) if rng is None else rng
+    k = np.empty((n, n, n))
+    th = n // layers
+    for z in range(n):
+        k[z] = lo if (z // th) % 2 == 0 else hi
+    corners = rng.integers(0, n - incl_size + 1, size=(incl, 3))
+    for cz, cy, cx in corners:
+        k[cz:cz + incl_size, cy:cy + incl_size, cx:cx + incl_size] = incl_val
+    return k.reshape(-1)
+
+
+def gaussian_field(n, seed, ell=0.1, rng=None, chunk=None):
+    """Seeded Gaussian random field on an n^3 periodic grid of the unit cube:
+    white noise N(0,1) per cell filtered by a Gaussian kernel of standard
+    deviation ell/sqrt(2) (covariance ~ exp(-r^2 / (2 ell^2)) up to the periodic
+    wrap), normalised to unit sample standard deviation.  Returned with x
+    fastest as float64, shape (n^3,)."""
+    rng = np.random.default_rng(seed) if rng is None else rng
+    w = rng.standard_normal((n, n, n), dtype=np.float64)
+    sigma = ell / np.sqrt(2.0)
+    f = np.fft.fftfreq(n)  # cycles per cell
+    # Gaussian transfer function exp(-2 pi^2 sigma^2 k^2) with k in cycles per unit length
+    g1 = np.exp(-2.0 * np.pi ** 2 * (sigma * n) ** 2 * f ** 2)
+    W = np.fft.rfftn(w)
+    del w
+    g_last = g1[: W.shape[2]]
+    W *= g1[:, None, None]
+    W *= g1[None, :, None]
+    W *= g_last[None, None, :]
+    g = np.fft.irfftn(W, s=(n, n, n))
+    del W
+    g -= g.mean()
+    g /= g.std()
+    return g.reshape(-1)
+
+
+def kappa_grf(n, seed, exponent=3.0, ell=0.1, rng=None):
+    """kappa = 10^(exponent * clip(g, -1, 1)), g = gaussian_field."""
+    g = gaussian_field(n, seed, ell=ell, rng=rng)
+    np.clip(g, -1.0, 1.0, out=g)
+    return np.power(10.0, exponent * g)
+
+
+def rhs_normal(npts, rng):
+    return rng.standard_normal(npts)
+
+
+def workload_blocks32(seed=0, n=32):
+    rng = np.random.default_rng(seed)
+    grid = (n, n, n)
+    kappa = kappa_blocks(grid, 4, seed, rng=rng)
+    b = rhs_normal(n ** 3, rng)
+    return dict(name=f"blocks{n}", grid=grid, kappa=kappa, bc=BC_Z_DIRICHLET, b=b)
+
+
+def workload_layered128(seed=0, n=128):
+    rng = np.random.default_rng(seed)
+    grid = (n, n, n)
+    kappa = kappa_layered(n, seed, rng=rng, layers=16, incl_size=max(1, n // 8))
+    h = 1.0 / n
+    b = np.full(n ** 3, h ** 3)
+    return dict(name=f"layered{n}", grid=grid, kappa=kappa, bc=BC_Z_DIRICHLET, b=b)
+
+
+def workload_grf(seed=0, n=350, exponent=3.0):
+    rng = np.random.default_rng(seed)
+    grid = (n, n, n)
+    kappa = kappa_grf(n, seed, exponent=exponent, rng=rng)
+    b = rhs_normal(n ** 3, rng)
+    return dict(name=f"grf{n}", grid=grid, kappa=kappa, bc=BC_Z_DIRICHLET, b=b)
+
+
+def workload_batched(seed=0, count=64, nrhs=4, lo=48, hi=160):
+    """Instance i uses seed + i: sizes first, then its 8x8x8-block kappa, then
+    its nrhs right-hand sides."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed + i)
+        nx, ny, nz = (int(v) for v in rng.integers(lo, hi + 1, size=3))
+        kappa = kappa_blocks((nx, ny, nz), 8, None, rng=rng)
+        bs = np.stack([rhs_normal(nx * ny * nz, rng) for _ in range(nrhs)])
+        out.append(dict(name=f"inst{i}", grid=(nx, ny, nz), kappa=kappa, bc=BC_Z_DIRICHLET, b=bs))
+    return out
+
+
+def random_small(grid, seed, contrast_exp=3, bc=BC_Z_DIRICHLET, per_cell=False):
+    """Small seeded instance for tests: block (2x2x2) or per-cell kappa
+    10^U[-c, c], b ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    n = int(np.prod(grid))
+    if per_cell:
+        kappa = np.power(10.0, rng.uniform(-contrast_exp, contrast_exp, n))
+    else:
+        kappa = kappa_blocks(grid, 2, None, emin=-contrast_exp, emax=contrast_exp, rng=rng)
+    b = rng.standard_normal(n)
+    return dict(name=f"rand{grid}", grid=tuple(grid), kappa=kappa, bc=tuple(bc), b=b)
