@@ -441,6 +441,79 @@ int or_setup(int nx, int ny, int nz, const double *d, const double *cx, const do
     return st;
 }
 
+
+/* ------------------------------------------------------------------ */
+/* ILU(0) smoother and the combination preconditioner B_c (Sec. III,   */
+/* "Smoothing high frequency components of error", Eq. (com))          */
+/* ------------------------------------------------------------------ */
+
+/* ILU(0) of the block-diagonal approximation blkD(A(1:M,1:M), A(M+1:N,M+1:N)),
+ * M = floor(N/2).  In natural order the 7-point pattern produces no fill that
+ * ILU(0) keeps, so the factorization only changes the pivots:
+ *   D_a = A_aa - sum over the lower neighbours b of a in the same block of A_ab^2 / D_b,
+ * and B_ILU0 = (D + L) D^{-1} (D + U), L / U the strict lower / upper parts of blkD(A). */
+int or_ilu0_setup(int nx, int ny, int nz, const double *d, const double *cx, const double *cy,
+                  const double *cz, double *D)
+{
+    const long nxy = (long)nx * ny, n = nxy * nz, M = n / 2;
+    for (long a = 0; a < n; ++a) {
+        const int ix = (int)(a % nx), iy = (int)((a / nx) % ny), iz = (int)(a / nxy);
+        const long lo = (a < M) ? 0 : M;           /* first row of a's block */
+        double v = d[a];
+        if (ix > 0 && a - 1 >= lo) v -= cx[a - 1] * cx[a - 1] / D[a - 1];
+        if (iy > 0 && a - nx >= lo) v -= cy[a - nx] * cy[a - nx] / D[a - nx];
+        if (iz > 0 && a - nxy >= lo) v -= cz[a - nxy] * cz[a - nxy] / D[a - nxy];
+        if (bad(v)) return OR_ERR_BREAKDOWN;
+        D[a] = v;
+    }
+    return OR_OK;
+}
+
+/* z = B_ILU0^{-1} r: forward sweep (D + L) y = r, backward sweep (I + D^{-1} U) z = y. */
+int or_ilu0_solve(int nx, int ny, int nz, const double *cx, const double *cy, const double *cz,
+                  const double *D, const double *r, double *z)
+{
+    const long nxy = (long)nx * ny, n = nxy * nz, M = n / 2;
+    for (long a = 0; a < n; ++a) {
+        const int ix = (int)(a % nx), iy = (int)((a / nx) % ny), iz = (int)(a / nxy);
+        const long lo = (a < M) ? 0 : M;
+        double v = r[a];
+        if (ix > 0 && a - 1 >= lo) v -= cx[a - 1] * z[a - 1];
+        if (iy > 0 && a - nx >= lo) v -= cy[a - nx] * z[a - nx];
+        if (iz > 0 && a - nxy >= lo) v -= cz[a - nxy] * z[a - nxy];
+        z[a] = v / D[a];
+    }
+    for (long a = n - 1; a >= 0; --a) {
+        const int ix = (int)(a % nx), iy = (int)((a / nx) % ny), iz = (int)(a / nxy);
+        const long hi = (a < M) ? M : n;             /* one past the last row of a's block */
+        double v = 0.0;
+        if (ix + 1 < nx && a + 1 < hi) v += cx[a] * z[a + 1];
+        if (iy + 1 < ny && a + nx < hi) v += cy[a] * z[a + nx];
+        if (iz + 1 < nz && a + nxy < hi) v += cz[a] * z[a + nxy];
+        z[a] -= v / D[a];
+    }
+    return OR_OK;
+}
+
+/* B_c^{-1} r = B_NTD^{-1} r + B_ILU0^{-1} r - B_NTD^{-1} A B_ILU0^{-1} r
+ *            = y1 + B_NTD^{-1} (r - A y1),  y1 = B_ILU0^{-1} r. */
+int or_combo_apply(int nx, int ny, int nz, const double *d, const double *cx, const double *cy,
+                   const double *cz, const double *l2, const double *l1, const double *M,
+                   const double *Dilu, const double *r, double *z)
+{
+    const long n = (long)nx * ny * nz;
+    double *y1 = (double *)malloc(sizeof(double) * n * 2);
+    if (!y1) return OR_ERR_ALLOC;
+    double *w = y1 + n;
+    or_ilu0_solve(nx, ny, nz, cx, cy, cz, Dilu, r, y1);
+    or_spmv(nx, ny, nz, d, cx, cy, cz, y1, w);
+    for (long e = 0; e < n; ++e) w[e] = r[e] - w[e];
+    or_apply(nx, ny, nz, cz, l2, l1, M, w, z);
+    for (long e = 0; e < n; ++e) z[e] += y1[e];
+    free(y1);
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* PCG / flexible CG (Sec. III conventions, readings R17 and R19)      */
 /* ------------------------------------------------------------------ */
@@ -454,7 +527,7 @@ static double dot(long n, const double *a, const double *b)
 
 int or_pcg(int nx, int ny, int nz, const double *d, const double *cx, const double *cy,
            const double *cz, const double *l2, const double *l1, const double *M,
-           const double *b, double *x, double rtol, int maxit, int flexible,
+           const double *Dilu, const double *b, double *x, double rtol, int maxit, int flexible,
            int *iters_out, double *relres_out, double *alpha_hist, double *beta_hist,
            double *res_hist)
 {
@@ -487,7 +560,8 @@ int or_pcg(int nx, int ny, int nz, const double *d, const double *cx, const doub
             fresh = 1;
         }
         if (it >= maxit) { st = OR_ERR_NOT_CONVERGED; break; }
-        or_apply(nx, ny, nz, cz, l2, l1, M, r, z);
+        if (Dilu) or_combo_apply(nx, ny, nz, d, cx, cy, cz, l2, l1, M, Dilu, r, z);
+        else or_apply(nx, ny, nz, cz, l2, l1, M, r, z);
         const double rho_new = dot(n, r, z);
         if (fresh) {
             for (long e = 0; e < n; ++e) p[e] = z[e];

@@ -20,9 +20,16 @@ int or_apply(int nx, int ny, int nz, const double *l3, const double *l2, const d
              const double *M, const double *r, double *z);
 int or_pcg(int nx, int ny, int nz, const double *d, const double *cx, const double *cy,
            const double *cz, const double *l2, const double *l1, const double *M,
-           const double *b, double *x, double rtol, int maxit, int flexible,
+           const double *Dilu, const double *b, double *x, double rtol, int maxit, int flexible,
            int *iters_out, double *relres_out, double *alpha_hist, double *beta_hist,
            double *res_hist);
+int or_ilu0_setup(int nx, int ny, int nz, const double *d, const double *cx, const double *cy,
+                  const double *cz, double *D);
+int or_ilu0_solve(int nx, int ny, int nz, const double *cx, const double *cy, const double *cz,
+                  const double *D, const double *r, double *z);
+int or_combo_apply(int nx, int ny, int nz, const double *d, const double *cx, const double *cy,
+                   const double *cz, const double *l2, const double *l1, const double *M,
+                   const double *Dilu, const double *r, double *z);
 #ifdef __cplusplus
 }
 #endif

@@ -54,9 +54,13 @@ def _load():
             lib.or_spmv.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D]
             lib.or_setup.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
             lib.or_apply.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D]
-            lib.or_pcg.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D, _D, _D, _D, d, i, i,
+            lib.or_pcg.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, d, i, i,
                                    ctypes.POINTER(i), ctypes.POINTER(d), _D, _D, _D]
-            for f in (lib.or_assemble, lib.or_spmv, lib.or_setup, lib.or_apply, lib.or_pcg):
+            lib.or_ilu0_setup.argtypes = [i, i, i, _D, _D, _D, _D, _D]
+            lib.or_ilu0_solve.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D]
+            lib.or_combo_apply.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+            for f in (lib.or_assemble, lib.or_spmv, lib.or_setup, lib.or_apply, lib.or_pcg,
+                      lib.or_ilu0_setup, lib.or_ilu0_solve, lib.or_combo_apply):
                 f.restype = i
             _lib = lib
     return _lib
@@ -138,8 +142,36 @@ def apply(f: Factors, r):
     return z
 
 
-def pcg(grid, bands, f: Factors, b, x0=None, rtol=1e-8, maxit=200, flexible=False):
-    """Returns dict(x, iters, relres, status, alpha, beta, res)."""
+def ilu0_setup(grid, bands):
+    """Pivots D of ILU(0) of blkD(A) (Sec. III, the smoother of the combination)."""
+    nx, ny, nz = grid
+    D = np.empty(nx * ny * nz)
+    _check(_load().or_ilu0_setup(nx, ny, nz, *[_p(b) for b in bands], _p(D)), "or_ilu0_setup")
+    return D
+
+
+def ilu0_solve(grid, bands, D, r):
+    nx, ny, nz = grid
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1)
+    z = np.empty_like(r)
+    _check(_load().or_ilu0_solve(nx, ny, nz, _p(bands[1]), _p(bands[2]), _p(bands[3]), _p(D),
+                                 _p(r), _p(z)), "or_ilu0_solve")
+    return z
+
+
+def combo_apply(grid, bands, f: Factors, D, r):
+    """B_c^{-1} r = B_NTD^{-1} r + B_ILU0^{-1} r - B_NTD^{-1} A B_ILU0^{-1} r (Sec. III Eq. (com))."""
+    nx, ny, nz = grid
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1)
+    z = np.empty_like(r)
+    _check(_load().or_combo_apply(nx, ny, nz, *[_p(b) for b in bands], _p(f.l2), _p(f.l1),
+                                  _p(f.M), _p(D), _p(r), _p(z)), "or_combo_apply")
+    return z
+
+
+def pcg(grid, bands, f: Factors, b, x0=None, rtol=1e-8, maxit=200, flexible=False, ilu=None):
+    """PCG with B_NTD, or with the combination B_c when ilu (pivots of
+    ilu0_setup) is given.  Returns dict(x, iters, relres, status, alpha, beta, res)."""
     nx, ny, nz = grid
     b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64).reshape(-1)
@@ -147,7 +179,7 @@ def pcg(grid, bands, f: Factors, b, x0=None, rtol=1e-8, maxit=200, flexible=Fals
     rr = ctypes.c_double(0.0)
     ah, bh, rh = np.zeros(maxit + 1), np.zeros(maxit + 1), np.zeros(maxit + 1)
     st = _load().or_pcg(nx, ny, nz, *[_p(v) for v in bands], _p(f.l2), _p(f.l1), _p(f.M),
-                        _p(b), _p(x), float(rtol), int(maxit), int(bool(flexible)),
+                        _p(ilu), _p(b), _p(x), float(rtol), int(maxit), int(bool(flexible)),
                         ctypes.byref(it), ctypes.byref(rr), _p(ah), _p(bh), _p(rh))
     k = it.value
     return dict(x=x, iters=k, relres=rr.value, status=st, alpha=ah[:k].copy(),

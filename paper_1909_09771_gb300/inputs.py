@@ -75,7 +75,7 @@ def gaussian_field(n, seed, ell=0.1, rng=None, chunk=None):
     W *= g1[:, None, None]
     W *= g1[None, :, None]
     W *= g_last[None, None, :]
-    g = np.fft.irfftn(W, s=(n, n, n))
+    g = np.fft.irfftn(W, s=(n, n, n), axes=(0, 1, 2))
     del W
     g -= g.mean()
     g /= g.std()

@@ -40,6 +40,14 @@ MUTATIONS = {
     "dirichlet_full_cell": ("else if (bc[0] == 0) diag += 2.0 * ka * ax;", "else if (bc[0] == 0) diag += ka * ax;"),
     # CG beta
     "cg_beta_inverted": ("else beta = rho_new / rho;", "else beta = rho / rho_new;"),
+    # ILU(0) pivots keep only the lower-neighbour terms of the same block
+    "ilu_ignores_block_split": ("if (iz > 0 && a - nxy >= lo) v -= cz[a - nxy] * cz[a - nxy] / D[a - nxy];",
+                                "if (iz > 0) v -= cz[a - nxy] * cz[a - nxy] / D[a - nxy];"),
+    # ILU(0) backward sweep divides by the pivot
+    "ilu_backward_no_pivot": ("        z[a] -= v / D[a];", "        z[a] -= v;"),
+    # combination: B_NTD acts on the residual of the smoother (Eq. (com))
+    "combo_drops_residual": ("for (long e = 0; e < n; ++e) w[e] = r[e] - w[e];",
+                             "for (long e = 0; e < n; ++e) w[e] = r[e];"),
 }
 
 
