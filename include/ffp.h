@@ -1,0 +1,167 @@
+/*
+ * ffp.h -- C ABI of the GB300 (sm_103a) library libffp.so: preconditioned
+ * conjugate gradients for the variable-coefficient 7-point finite-volume
+ * diffusion operator on a structured 3-D grid, preconditioned by the nested
+ * twisted frequency-filtering preconditioner (NTD) of arXiv 1909.09771.
+ *
+ * Conventions (all entry points)
+ *   - Grid index a = x + nx*(y + ny*z): x fastest, then y (lines), then z
+ *     (planes).  This is the ordering of the nested block-tridiagonal matrix
+ *     in Sec. II of the paper (nx cells per line, ny lines per plane, nz planes).
+ *   - Every vector argument is a DEVICE pointer to N = nx*ny*nz FP64 values,
+ *     owned by the caller; the library never allocates, frees or keeps device
+ *     memory beyond the caller's workspace, and never copies to the host
+ *     except the small status/scalar block of ffp_pcg_solve.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call enqueues its kernels on that stream; only
+ *     ffp_setup (status check) and ffp_pcg_solve (convergence checks)
+ *     synchronise it.
+ *   - Return value: FFP_OK (0) or a negative FFP_ERR_* code; ffp_strerror()
+ *     names it.  On an error the output buffers hold unspecified values.
+ *   - Only one GPU (the current device at ffp_setup) is used.
+ */
+#ifndef FFP_H
+#define FFP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FFP_OK 0
+#define FFP_ERR_ARG (-1)            /* bad argument: null pointer, n < 1, nx > FFP_MAX_NX,
+                                       kappa or t not positive and finite, workspace too small */
+#define FFP_ERR_CUDA (-2)           /* a CUDA runtime call failed */
+#define FFP_ERR_BREAKDOWN (-3)      /* a non-positive / non-finite pivot or diagonal in setup,
+                                       or (p, Ap) <= 0 in CG */
+#define FFP_ERR_NOT_CONVERGED (-4)  /* maxit reached; x holds the last iterate */
+#define FFP_ERR_UNSUPPORTED (-6)    /* the requested option is not available */
+
+#define FFP_MAX_NX 1024             /* longest line (cells along x) the line solvers support */
+
+/* boundary condition per face */
+#define FFP_DIRICHLET 0             /* u = 0 on the face (Sec. I Eq. (2)) */
+#define FFP_NEUMANN 1               /* du/dn = 0 on the face */
+
+/* filter vector t of the filtering property B t = A t (Sec. I Eq. (3)) */
+#define FFP_FILTER_ROWSUM 0         /* t = 1, the rowsum constraint (Sec. I Eq. (4)) */
+#define FFP_FILTER_USER 1           /* caller-supplied t, device FP64 [N], every entry > 0 */
+
+/* preconditioner */
+#define FFP_PRECOND_NTD 0           /* B_NTD, the nested twisted filtering preconditioner (Sec. II) */
+#define FFP_PRECOND_COMBO 1         /* B_c^{-1} = B_NTD^{-1} + B_ILU0^{-1} - B_NTD^{-1} A B_ILU0^{-1},
+                                       ILU(0) of blkD(A) split at M = floor(N/2) (Sec. III, Eq. (com)),
+                                       the preconditioner of the paper's experiments */
+
+/* storage and arithmetic precision of the preconditioner factors */
+#define FFP_FP64 0                  /* FP64 factors, FP64 apply, standard PCG (flexible CG with B_c) */
+#define FFP_FP32 1                  /* FP32 factors, FP32 apply, FP64 flexible CG */
+#define FFP_BF16 2                  /* BF16 factors, FP32 apply, FP64 flexible CG */
+
+/* Structured grid on the box [0,lx] x [0,ly] x [0,lz] (lengths <= 0 mean 1). */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz;
+} ffp_grid;
+
+/* Boundary flag per face, order x-, x+, y-, y+, z-, z+; FFP_DIRICHLET or FFP_NEUMANN. */
+typedef struct {
+    unsigned char face[6];
+} ffp_bc;
+
+/* Result of ffp_pcg_solve. */
+typedef struct {
+    int iters;            /* CG iterations (products A p) after the initial residual */
+    int status;           /* same value the call returns */
+    double rel_res;       /* recursive ||r|| / ||b|| at exit */
+    double rel_res_true;  /* ||b - A x|| / ||b|| recomputed at exit */
+    double solve_s;       /* wall time of the solve (host clock, after a stream sync) */
+} ffp_stats;
+
+typedef struct ffp_handle ffp_handle;
+
+/* Bytes of device workspace ffp_setup needs for this grid and factor precision
+ * (0 on a bad grid).  The workspace holds the operator bands, the factors, the
+ * CG vectors and small scratch; its base must be 256-byte aligned. */
+size_t ffp_workspace_bytes(const ffp_grid *grid, int precision);
+
+/* Assemble A from kappa and build the NTD preconditioner.
+ *
+ * Operator (Sec. I Eq. (2), finite-volume reading): face coefficient
+ * kappa_f * area / distance, kappa_f the harmonic mean 2 ka kb / (ka + kb)
+ * of the two cells; a Dirichlet face contributes 2 kappa * area / h (half a
+ * cell to the face); a Neumann face nothing; the diagonal is the sum of the
+ * cell's face coefficients.
+ *
+ * Preconditioner (Sec. II-A): twisted block factorizations at three nested
+ * levels -- planes (P_i recurrence with the approximate inverse
+ * 2 beta - beta P beta), lines of every plane (T_k recurrence, same form) and
+ * cells of every line (exact twisted pivots M_i) -- with the twist block
+ * m = floor((n-1)/2) at every level, beta = diag((X^{-1} w) ./ w), w = coupling
+ * times t restricted to the block being built; the plane inverse inside the
+ * level-3 beta is the nested level-2 solve of that plane.  With
+ * FFP_PRECOND_COMBO the ILU(0) pivots of blkD(A) are built too (Sec. III).
+ * The factors are computed in FP64 and stored in `precision`.
+ *
+ *   grid       nx, ny, nz >= 1, nx <= FFP_MAX_NX
+ *   kappa      device FP64 [N], > 0 and finite (else FFP_ERR_ARG)
+ *   bc         host pointer to the 6 face flags
+ *   filter     FFP_FILTER_ROWSUM (t ignored, may be NULL) or FFP_FILTER_USER
+ *   t          device FP64 [N] filter vector (entries > 0, else FFP_ERR_ARG)
+ *   precision  FFP_FP64, FFP_FP32 or FFP_BF16
+ *   precond    FFP_PRECOND_NTD or FFP_PRECOND_COMBO
+ *   workspace  device memory of ws_bytes >= ffp_workspace_bytes(grid, precision),
+ *              owned by the caller and kept alive until ffp_destroy
+ *   out        receives a host handle (freed by ffp_destroy)
+ * Synchronises `stream` once to read the setup status.  Returns
+ * FFP_ERR_BREAKDOWN if a pivot or diagonal is not positive and finite. */
+int ffp_setup(const ffp_grid *grid, const double *kappa, const ffp_bc *bc, int filter,
+              const double *t, int precision, int precond, void *workspace, size_t ws_bytes,
+              void *stream, ffp_handle **out);
+
+/* y = A x (device FP64 [N] each; x and y must not overlap).  Sec. II: the 7-point
+ * band storage of A. */
+int ffp_spmv(ffp_handle *h, const double *x, double *y, void *stream);
+
+/* z = B^{-1} r (device FP64 [N] each; r and z must not overlap).
+ * B_NTD: Sec. II-B Algorithms 1-7, SOLVE(1, N, x, y, n^2, 3) -- a twisted
+ * lower then upper sweep over planes, each plane solved by the same two sweeps
+ * over its lines, each line by the twisted tridiagonal solve.
+ * B_c (FFP_PRECOND_COMBO): y = B_ILU0^{-1} r, z = y + B_NTD^{-1} (r - A y).
+ * Arithmetic in FP64 (FFP_FP64) or FP32 (FFP_FP32, FFP_BF16). */
+int ffp_apply(ffp_handle *h, const double *r, double *z, void *stream);
+
+/* Solve A x = b by preconditioned CG (Sec. III: x0 given, stop when
+ * ||r|| / ||b|| < rtol, then confirm with the true residual ||b - A x|| / ||b||
+ * and continue from it if it is not below rtol; at most maxit iterations).
+ * FFP_FP64 with B_NTD runs standard PCG; FP32/BF16 factors or B_c (not
+ * symmetric) run flexible CG, beta = (z_new, r_new - r_old) / (z_old, r_old).  All CG vectors, dot
+ * products and scalars are FP64.
+ *   b      device FP64 [N]
+ *   x      device FP64 [N]: in x0, out the solution (b = 0 gives x = 0, 0 iterations)
+ *   stats  host pointer or NULL
+ * Returns FFP_ERR_NOT_CONVERGED at maxit, FFP_ERR_BREAKDOWN if (p, A p) <= 0. */
+int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int maxit,
+                  ffp_stats *stats, void *stream);
+
+/* Copy the stored operator and factors out as FP64 device arrays [N] each (any
+ * pointer may be NULL): d, cx, cy, cz = bands of A (cx[a] = A[a, a+1], cy[a] =
+ * A[a, a+nx], cz[a] = A[a, a+nx*ny], zero where there is no neighbour);
+ * l2 = y-band of every P_i, l1 = x-band of every T_k, minv = 1 / M (level-1
+ * pivots) -- the band storage of Sec. II-A, in the stored precision; dinv =
+ * 1 / D, the ILU(0) pivots (B_c only, else left untouched). */
+int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, double *l2,
+               double *l1, double *minv, double *dinv, void *stream);
+
+/* Free the host handle (no device memory is freed). */
+void ffp_destroy(ffp_handle *h);
+
+/* Static text for a status code. */
+const char *ffp_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFP_H */

@@ -1,0 +1,286 @@
+// ffp_api.cu -- the C ABI declared in include/ffp.h.
+//
+// The caller owns every device buffer, including the workspace, which this
+// file carves into the operator bands, the stored factors, the CG vectors and
+// small scratch; the handle is a host struct that only points into it.
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "ffp_kernels.h"
+
+using namespace ffp;
+
+struct ffp_handle {
+    KernelCtx c;
+    int device;
+    double *host_scal;  // pinned copy of the scalar block + flags
+};
+
+namespace {
+
+size_t prec_bytes(int prec) {
+    switch (prec) {
+        case FFP_FP64: return 8;
+        case FFP_FP32: return 4;
+        case FFP_BF16: return 2;
+        default: return 0;
+    }
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+bool grid_ok(const ffp_grid *g) {
+    if (!g || g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nx > FFP_MAX_NX) return false;
+    const long long n = (long long)g->nx * g->ny * g->nz;
+    return n <= 2000000000LL;
+}
+
+// Carve the workspace (base may be 0 to compute the size).  Returns the total size.
+size_t carve(const ffp_grid *g, int prec, char *base, Ws *ws) {
+    const size_t n = (size_t)g->nx * g->ny * g->nz;
+    const size_t nxy = (size_t)g->nx * g->ny;
+    const size_t fb = prec_bytes(prec);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += align_up(bytes);
+        return p;
+    };
+    Ws w;
+    std::memset(&w, 0, sizeof(w));
+    w.d = (double *)take(8 * n); w.cx = (double *)take(8 * n);
+    w.cy = (double *)take(8 * n); w.cz = (double *)take(8 * n);
+    w.l1 = take(fb * n); w.minv = take(fb * n); w.l2 = take(fb * n); w.l3 = take(fb * n);
+    w.dinv = take(fb * n); w.lx = take(fb * n); w.ly = take(fb * n);
+    w.r = (double *)take(8 * n); w.z = (double *)take(8 * n);
+    w.p = (double *)take(8 * n); w.q = (double *)take(8 * n);
+    w.c1 = (double *)take(8 * n); w.c2 = (double *)take(8 * n);
+    w.ascr = (double *)take(8 * 2 * nxy);
+    for (int h = 0; h < 2; ++h) {
+        for (int pp = 0; pp < 2; ++pp)
+            for (int b = 0; b < 3; ++b) w.sP[h][pp][b] = (double *)take(8 * nxy);
+        for (int b = 0; b < 2; ++b) w.sF[h][b] = (double *)take(8 * nxy);
+        for (int b = 0; b < 2; ++b) w.sW[h][b] = (double *)take(8 * nxy);
+        for (int b = 0; b < 3; ++b) w.sC[h][b] = (double *)take(8 * nxy);
+    }
+    w.red = (double *)take(8 * (size_t)kRedSlots);
+    // scalar block and flags are contiguous so one copy brings both back
+    w.scal = (double *)take(8 * (size_t)kScal + 4 * 16);
+    w.flags = base ? (int *)(w.scal + kScal) : nullptr;
+    if (ws) *ws = w;
+    return off;
+}
+
+constexpr size_t kScalBytes = 8 * (size_t)kScal + 4 * 16;
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? FFP_OK : FFP_ERR_CUDA; }
+
+// z = B^{-1} r for the handle's preconditioner (r and z distinct from c1, c2)
+cudaError_t precond_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st) {
+    if (c.precond != FFP_PRECOND_COMBO) return launch_apply(c, r, z, st);
+    // B_c^{-1} r = y + B_NTD^{-1} (r - A y), y = B_ILU0^{-1} r
+    cudaError_t e = launch_ilu_solve(c, r, c.ws.c1, st);
+    if (e == cudaSuccess) e = launch_resid_vec(c, r, c.ws.c1, c.ws.c2, st);
+    if (e == cudaSuccess) e = launch_apply(c, c.ws.c2, z, st);
+    if (e == cudaSuccess) e = launch_add(c, z, c.ws.c1, st);
+    return e;
+}
+
+int read_scalars(ffp_handle *h, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(h->host_scal, h->c.ws.scal, kScalBytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return FFP_ERR_CUDA;
+    e = cudaStreamSynchronize(st);
+    return cuda_status(e);
+}
+
+const int *host_flags(const ffp_handle *h) { return (const int *)(h->host_scal + kScal); }
+
+}  // namespace
+
+extern "C" {
+
+size_t ffp_workspace_bytes(const ffp_grid *grid, int precision) {
+    if (!grid_ok(grid) || prec_bytes(precision) == 0) return 0;
+    return carve(grid, precision, nullptr, nullptr);
+}
+
+int ffp_setup(const ffp_grid *grid, const double *kappa, const ffp_bc *bc, int filter,
+              const double *t, int precision, int precond, void *workspace, size_t ws_bytes,
+              void *stream, ffp_handle **out) {
+    if (out) *out = nullptr;
+    if (!grid_ok(grid) || !kappa || !bc || !workspace || !out) return FFP_ERR_ARG;
+    if (prec_bytes(precision) == 0) return FFP_ERR_ARG;
+    if (filter != FFP_FILTER_ROWSUM && filter != FFP_FILTER_USER) return FFP_ERR_ARG;
+    if (precond != FFP_PRECOND_NTD && precond != FFP_PRECOND_COMBO) return FFP_ERR_ARG;
+    if (filter == FFP_FILTER_USER && !t) return FFP_ERR_ARG;
+    if (((uintptr_t)workspace & 255) != 0) return FFP_ERR_ARG;
+    for (int f = 0; f < 6; ++f)
+        if (bc->face[f] != FFP_DIRICHLET && bc->face[f] != FFP_NEUMANN) return FFP_ERR_ARG;
+    const size_t need = carve(grid, precision, nullptr, nullptr);
+    if (ws_bytes < need) return FFP_ERR_ARG;
+    const int slots = slots_for(grid->nx);
+    if (slots < 0) return FFP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    ffp_handle *h = new (std::nothrow) ffp_handle;
+    if (!h) return FFP_ERR_ARG;
+    std::memset(h, 0, sizeof(*h));
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return FFP_ERR_CUDA; }
+    if (cudaMallocHost((void **)&h->host_scal, kScalBytes) != cudaSuccess) { delete h; return FFP_ERR_CUDA; }
+    KernelCtx &c = h->c;
+    c.nx = grid->nx; c.ny = grid->ny; c.nz = grid->nz;
+    c.n = (long long)c.nx * c.ny * c.nz;
+    c.lx = grid->lx > 0 ? grid->lx : 1.0;
+    c.ly = grid->ly > 0 ? grid->ly : 1.0;
+    c.lz = grid->lz > 0 ? grid->lz : 1.0;
+    c.prec = precision;
+    c.precond = precond;
+    c.slots = slots;
+    carve(grid, precision, (char *)workspace, &c.ws);
+
+    cudaError_t e = cudaMemsetAsync(c.ws.scal, 0, kScalBytes, st);
+    if (e == cudaSuccess) e = launch_assemble(c, kappa, bc->face, st);
+    if (e == cudaSuccess && filter == FFP_FILTER_USER) e = launch_check_filter(c, t, st);
+    int status = cuda_status(e);
+    if (status == FFP_OK) status = read_scalars(h, st);
+    if (status == FFP_OK && host_flags(h)[FL_ARG]) status = FFP_ERR_ARG;
+    if (status == FFP_OK) {
+        e = launch_convert_bands(c, st);
+        if (e == cudaSuccess) e = launch_setup(c, filter == FFP_FILTER_USER ? t : nullptr, st);
+        // ILU(0) pivots in FP64 use the CG vector p as scratch (free until a solve)
+        if (e == cudaSuccess && precond == FFP_PRECOND_COMBO) e = launch_ilu_setup(c, c.ws.p, st);
+        status = cuda_status(e);
+    }
+    if (status == FFP_OK) status = read_scalars(h, st);
+    if (status == FFP_OK && host_flags(h)[FL_BREAKDOWN]) status = FFP_ERR_BREAKDOWN;
+    if (status != FFP_OK) {
+        ffp_destroy(h);
+        return status;
+    }
+    *out = h;
+    return FFP_OK;
+}
+
+int ffp_spmv(ffp_handle *h, const double *x, double *y, void *stream) {
+    if (!h || !x || !y) return FFP_ERR_ARG;
+    return cuda_status(launch_spmv(h->c, x, y, (cudaStream_t)stream));
+}
+
+int ffp_apply(ffp_handle *h, const double *r, double *z, void *stream) {
+    if (!h || !r || !z || r == z) return FFP_ERR_ARG;
+    return cuda_status(precond_apply(h->c, r, z, (cudaStream_t)stream));
+}
+
+int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, double *l2,
+               double *l1, double *minv, double *dinv, void *stream) {
+    if (!h) return FFP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nb = 8 * (size_t)h->c.n;
+    cudaError_t e = cudaSuccess;
+    if (d && e == cudaSuccess) e = cudaMemcpyAsync(d, h->c.ws.d, nb, cudaMemcpyDeviceToDevice, st);
+    if (cx && e == cudaSuccess) e = cudaMemcpyAsync(cx, h->c.ws.cx, nb, cudaMemcpyDeviceToDevice, st);
+    if (cy && e == cudaSuccess) e = cudaMemcpyAsync(cy, h->c.ws.cy, nb, cudaMemcpyDeviceToDevice, st);
+    if (cz && e == cudaSuccess) e = cudaMemcpyAsync(cz, h->c.ws.cz, nb, cudaMemcpyDeviceToDevice, st);
+    if (l2 && e == cudaSuccess) e = launch_export(h->c, h->c.ws.l2, l2, st);
+    if (l1 && e == cudaSuccess) e = launch_export(h->c, h->c.ws.l1, l1, st);
+    if (minv && e == cudaSuccess) e = launch_export(h->c, h->c.ws.minv, minv, st);
+    if (dinv && e == cudaSuccess && h->c.precond == FFP_PRECOND_COMBO)
+        e = launch_export(h->c, h->c.ws.dinv, dinv, st);
+    return cuda_status(e);
+}
+
+int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int maxit,
+                  ffp_stats *stats, void *stream) {
+    if (!h || !b || !x || !(rtol > 0.0) || maxit < 0) return FFP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const KernelCtx &c = h->c;
+    const int flexible = (c.prec != FFP_FP64) || (c.precond == FFP_PRECOND_COMBO);
+    auto t0 = std::chrono::steady_clock::now();
+    int it = 0, fresh = 1, status = FFP_OK;
+    double bb = 0.0, rr = 0.0;
+#define FFP_TRY(expr)                                                 \
+    do {                                                              \
+        cudaError_t _e = (expr);                                      \
+        if (_e != cudaSuccess) { status = FFP_ERR_CUDA; goto done; } \
+    } while (0)
+    FFP_TRY(cudaMemsetAsync(c.ws.flags, 0, 4 * 16, st));
+    FFP_TRY(launch_resid(c, b, x, st));
+    FFP_TRY(launch_finalize(c, FIN_RESID, 0, flexible, st));
+    if ((status = read_scalars(h, st)) != FFP_OK) goto done;
+    bb = h->host_scal[SC_BB];
+    rr = h->host_scal[SC_RR];
+    if (bb == 0.0) {
+        FFP_TRY(cudaMemsetAsync(x, 0, 8 * (size_t)c.n, st));
+        if (stats) {
+            stats->iters = 0; stats->status = FFP_OK; stats->rel_res = 0.0;
+            stats->rel_res_true = 0.0; stats->solve_s = 0.0;
+        }
+        cudaStreamSynchronize(st);
+        return FFP_OK;
+    }
+    for (;;) {
+        if (std::sqrt(rr / bb) < rtol) {
+            // confirm with the true residual; continue from it if it is not converged
+            FFP_TRY(launch_resid(c, b, x, st));
+            FFP_TRY(launch_finalize(c, FIN_RESID, 0, flexible, st));
+            if ((status = read_scalars(h, st)) != FFP_OK) goto done;
+            rr = h->host_scal[SC_RR];
+            if (std::sqrt(rr / bb) < rtol) break;
+            fresh = 1;
+        }
+        if (it >= maxit) { status = FFP_ERR_NOT_CONVERGED; break; }
+        FFP_TRY(precond_apply(c, c.ws.r, c.ws.z, st));
+        FFP_TRY(launch_dot_rz(c, st));
+        FFP_TRY(launch_finalize(c, FIN_RZ, fresh, flexible, st));
+        FFP_TRY(launch_update_p(c, fresh, st));
+        fresh = 0;
+        FFP_TRY(launch_spmv_dot(c, st));
+        FFP_TRY(launch_finalize(c, FIN_PQ, 0, flexible, st));
+        FFP_TRY(launch_update_xr(c, x, st));
+        FFP_TRY(launch_finalize(c, FIN_RR, 0, flexible, st));
+        ++it;
+        if ((status = read_scalars(h, st)) != FFP_OK) goto done;
+        if (host_flags(h)[FL_PQ]) { status = FFP_ERR_BREAKDOWN; break; }
+        rr = h->host_scal[SC_RR];
+        if (!std::isfinite(rr)) { status = FFP_ERR_BREAKDOWN; break; }
+    }
+done:
+#undef FFP_TRY
+    if (stats) {
+        stats->iters = it;
+        stats->status = status;
+        stats->rel_res = (bb > 0.0) ? std::sqrt(rr / bb) : 0.0;
+        stats->rel_res_true = -1.0;
+        if (status != FFP_ERR_CUDA) {
+            if (launch_resid(c, b, x, st) == cudaSuccess &&
+                launch_finalize(c, FIN_RESID, 0, flexible, st) == cudaSuccess &&
+                read_scalars(h, st) == FFP_OK)
+                stats->rel_res_true = std::sqrt(h->host_scal[SC_TRR] / bb);
+        }
+        stats->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
+}
+
+void ffp_destroy(ffp_handle *h) {
+    if (!h) return;
+    if (h->host_scal) cudaFreeHost(h->host_scal);
+    delete h;
+}
+
+const char *ffp_strerror(int status) {
+    switch (status) {
+        case FFP_OK: return "ok";
+        case FFP_ERR_ARG: return "invalid argument";
+        case FFP_ERR_CUDA: return "CUDA runtime error";
+        case FFP_ERR_BREAKDOWN: return "breakdown: non-positive pivot or (p, Ap) <= 0";
+        case FFP_ERR_NOT_CONVERGED: return "not converged within maxit";
+        case FFP_ERR_UNSUPPORTED: return "unsupported option";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,9 @@
+// Explicit instantiations of the apply kernels for __nv_bfloat16 factors (one TU per
+// storage precision so the build compiles them in parallel).
+#include "ffp_apply.cuh"
+
+namespace ffp {
+#define FFP_INST(SS) template cudaError_t apply_for_slots<SS, __nv_bfloat16>(const KernelCtx &, const double *, double *, cudaStream_t);
+FFP_SLOT_LIST(FFP_INST)
+#undef FFP_INST
+}  // namespace ffp

@@ -1,0 +1,327 @@
+// ffp_internal.cuh -- device building blocks shared by the kernels of libffp.so.
+//
+// Line layout inside a warp (level 1 of the nested preconditioner, Sec. II-A):
+// a line of n cells is split at the twist cell m = floor((n-1)/2).  The top
+// chain is cells 0..m-1 (eliminated from cell 0 towards m), the bottom chain is
+// cells n-1..m+1 (eliminated from n-1 towards m).  Lanes 0-15 hold the top
+// chain and lanes 16-31 the bottom chain; within a half, lane j holds the
+// chain positions c = j*S .. j*S+S-1 in registers ("slots"), so both chains
+// are handled by 16-lane affine scans running side by side, which is the
+// two-way parallelism the twist exposes.  Chain position c maps to cell
+// a = c (top) or a = n-1-c (bottom).  Slots past the end of a chain are
+// identity steps (pads).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/ffp.h"
+
+namespace ffp {
+
+// ---------------------------------------------------------------- storage types
+template <typename F> struct Compute { using type = float; };
+template <> struct Compute<double> { using type = double; };
+
+__device__ __forceinline__ double to_r(double v, double) { return v; }
+__device__ __forceinline__ float to_r(float v, float) { return v; }
+__device__ __forceinline__ float to_r(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_r(double v, float) { return (float)v; }
+
+template <typename F> __device__ __forceinline__ F from_d(double v);
+template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_d<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) {
+    return __double2bfloat16(v);
+}
+
+// Factor loads.  NC = true: through the read-only (non-coherent) path, for
+// data no thread writes while the kernel runs; NC = false: coherent loads, for
+// buffers the same kernel rewrites (setup scratch).
+template <bool NC, typename F, typename R>
+__device__ __forceinline__ R ldf(const F *p) {
+    if constexpr (NC) return to_r(__ldg(p), R());
+    else return to_r(*p, R());
+}
+
+// ---------------------------------------------------------------- line geometry
+struct LineMap {
+    int n;     // cells in the line
+    int m;     // twist cell
+    int ntop;  // cells in the top chain (= m)
+    int nbot;  // cells in the bottom chain (= n-1-m)
+    __device__ __forceinline__ explicit LineMap(int n_) : n(n_), m((n_ - 1) / 2) {
+        ntop = m;
+        nbot = n_ - 1 - m;
+    }
+};
+
+// Number of valid slots of this lane (slots >= cnt are pads).
+template <int S>
+__device__ __forceinline__ int lane_count(const LineMap &L, int lane) {
+    const int j = lane & 15;
+    const int tot = (lane < 16) ? L.ntop : L.nbot;
+    int c = tot - j * S;
+    return c < 0 ? 0 : (c > S ? S : c);
+}
+
+// Cell index of slot s of this lane (only meaningful for valid slots).
+template <int S>
+__device__ __forceinline__ int slot_cell(const LineMap &L, int lane, int s) {
+    const int c = (lane & 15) * S + s;
+    return (lane < 16) ? c : L.n - 1 - c;
+}
+
+// Coefficients of one twisted tridiagonal factor T = (M + L1) M^{-1} (M + U1)
+// as seen from this lane: minv = 1/M per slot, ein = coupling to the chain
+// predecessor, eout = coupling towards the twist cell; plus the twist cell.
+template <int S, typename R>
+struct LineFactor {
+    R minv[S], ein[S], eout[S];
+    R minv_m;  // 1 / M_m
+    R em1;     // T[m-1, m] (0 if m == 0)
+    R em;      // T[m, m+1] (0 if m == n-1)
+};
+
+// Load the factor of one line from band arrays l1 (x-band, l1[a] couples a and
+// a+1, 0 at a = n-1) and minv (1/M), both indexed by cell of this line.
+template <int S, bool NC, typename F, typename R>
+__device__ __forceinline__ void load_line_factor(const LineMap &L, int lane, int cnt,
+                                                 const F *__restrict__ l1,
+                                                 const F *__restrict__ minv,
+                                                 LineFactor<S, R> &f) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (s < cnt) {
+            const int a = slot_cell<S>(L, lane, s);
+            const R e_lo = (a > 0) ? ldf<NC, F, R>(l1 + a - 1) : R(0);  // couples a-1, a
+            const R e_hi = ldf<NC, F, R>(l1 + a);                       // couples a, a+1
+            f.minv[s] = ldf<NC, F, R>(minv + a);
+            if (lane < 16) { f.ein[s] = e_lo; f.eout[s] = e_hi; }
+            else { f.ein[s] = e_hi; f.eout[s] = e_lo; }
+        } else {
+            f.minv[s] = R(0); f.ein[s] = R(0); f.eout[s] = R(0);
+        }
+    }
+    f.minv_m = ldf<NC, F, R>(minv + L.m);
+    f.em1 = (L.m > 0) ? ldf<NC, F, R>(l1 + L.m - 1) : R(0);
+    f.em = ldf<NC, F, R>(l1 + L.m);
+}
+
+// ---------------------------------------------------------------- level-1 solve
+// Solve T x = b for one line with the twisted factorization of Sec. II-A
+// (level 1): lower sweep (M + L1) y = b from both ends towards the twist cell,
+// the twist cell takes both couplings, then the upper sweep (I + M^{-1} U1) x = y
+// from the twist cell outwards.  Each sweep is a first-order affine recurrence
+// along a chain, evaluated as lane-local composition + a 16-lane scan +
+// lane-local substitution.  b/x are per-slot registers; bm/xm the twist cell.
+// x may alias b.
+template <int S, typename R>
+__device__ __forceinline__ void twisted_solve(const LineFactor<S, R> &f, int cnt, int lane,
+                                              const R (&b)[S], R bm, R (&x)[S], R &xm) {
+    const int j = lane & 15;
+    const unsigned FULL = 0xffffffffu;
+    // ---- lower sweep: y[c] = minv (b - ein y[c-1]) = al * y[c-1] + be
+    R al[S];
+    R A = R(1), B = R(0);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const bool v = s < cnt;
+        const R a_ = v ? -f.minv[s] * f.ein[s] : R(1);
+        const R be = v ? f.minv[s] * b[s] : R(0);
+        al[s] = a_;
+        x[s] = be;
+        B = fma(a_, B, be);
+        A = A * a_;
+    }
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const R Au = __shfl_up_sync(FULL, A, d, 16);
+        const R Bu = __shfl_up_sync(FULL, B, d, 16);
+        if (j >= d) { B = fma(A, Bu, B); A = A * Au; }
+    }
+    R c = __shfl_up_sync(FULL, B, 1, 16);
+    if (j == 0) c = R(0);
+#pragma unroll
+    for (int s = 0; s < S; ++s) { c = fma(al[s], c, x[s]); x[s] = c; }
+    const R ytop = __shfl_sync(FULL, B, 15);   // y at cell m-1 (0 if the top chain is empty)
+    const R ybot = __shfl_sync(FULL, B, 31);   // y at cell m+1
+    const R ym = f.minv_m * (bm - f.em1 * ytop - f.em * ybot);
+    // ---- upper sweep: x[c] = y[c] - minv eout x[c+1] = y[c] + ga * x[c+1], x[end] = xm
+    R ga[S];
+    R G = R(1);
+    B = R(0);
+#pragma unroll
+    for (int s = S - 1; s >= 0; --s) {
+        const bool v = s < cnt;
+        const R g_ = v ? -f.minv[s] * f.eout[s] : R(1);
+        const R yy = v ? x[s] : R(0);
+        ga[s] = g_;
+        x[s] = yy;
+        B = fma(g_, B, yy);
+        G = G * g_;
+    }
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const R Gd = __shfl_down_sync(FULL, G, d, 16);
+        const R Bd = __shfl_down_sync(FULL, B, d, 16);
+        if (j + d < 16) { B = fma(G, Bd, B); G = G * Gd; }
+    }
+    const R Gn = __shfl_down_sync(FULL, G, 1, 16);
+    const R Bn = __shfl_down_sync(FULL, B, 1, 16);
+    c = (j == 15) ? ym : fma(Gn, ym, Bn);
+#pragma unroll
+    for (int s = S - 1; s >= 0; --s) { c = fma(ga[s], c, x[s]); x[s] = c; }
+    xm = ym;
+}
+
+// ---------------------------------------------------------------- level-1 pivots
+// Twisted pivots of the tridiagonal T (recurrence for M_i, Sec. II-A):
+// M[c] = D[c] - ein[c]^2 / M[c-1] along each chain, and at the twist cell
+// M_m = D_m - em1^2 / M_{m-1} - em^2 / M_{m+1}.  The continued fraction is
+// evaluated projectively: M = p/q with (p, q) <- (D p - e^2 q, p), i.e. a
+// product of 2x2 matrices, scanned across the 16 lanes of a chain (scaled by
+// powers of two, which leaves p/q unchanged) and then substituted slot by
+// slot from the lane's incoming (p, q).  FP64.  Returns 1/M per slot and for
+// the twist cell; `bad` is set if a pivot is not positive and finite.
+__device__ __forceinline__ void scale4(double &a, double &b, double &c, double &d) {
+    const double mx = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(c), fabs(d)));
+    if (mx > 0.0 && isfinite(mx)) {
+        const int e = ilogb(mx);
+        a = scalbn(a, -e); b = scalbn(b, -e); c = scalbn(c, -e); d = scalbn(d, -e);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void twisted_pivots(int cnt, int lane, const double (&D)[S],
+                                               const double (&ein)[S], double Dm, double em1,
+                                               double em, double (&minv)[S], double &minv_m,
+                                               bool &bad) {
+    const int j = lane & 15;
+    const unsigned FULL = 0xffffffffu;
+    // lane-local product P = E_{S-1} ... E_0, E = [[D, -e^2], [1, 0]]
+    double p11 = 1.0, p12 = 0.0, p21 = 0.0, p22 = 1.0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (s < cnt) {
+            const double e2 = ein[s] * ein[s];
+            const double n11 = D[s] * p11 - e2 * p21;
+            const double n12 = D[s] * p12 - e2 * p22;
+            p21 = p11; p22 = p12; p11 = n11; p12 = n12;
+        }
+    }
+    scale4(p11, p12, p21, p22);
+    // inclusive scan: lane j <- (lane j) x (lane j-d)
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const double q11 = __shfl_up_sync(FULL, p11, d, 16);
+        const double q12 = __shfl_up_sync(FULL, p12, d, 16);
+        const double q21 = __shfl_up_sync(FULL, p21, d, 16);
+        const double q22 = __shfl_up_sync(FULL, p22, d, 16);
+        if (j >= d) {
+            const double n11 = p11 * q11 + p12 * q21;
+            const double n12 = p11 * q12 + p12 * q22;
+            const double n21 = p21 * q11 + p22 * q21;
+            const double n22 = p21 * q12 + p22 * q22;
+            p11 = n11; p12 = n12; p21 = n21; p22 = n22;
+            scale4(p11, p12, p21, p22);
+        }
+    }
+    // incoming (p, q) = first column of the prefix of lane j-1 ((1, 0) for lane 0)
+    double pp = __shfl_up_sync(FULL, p11, 1, 16);
+    double qq = __shfl_up_sync(FULL, p21, 1, 16);
+    if (j == 0) { pp = 1.0; qq = 0.0; }
+    {
+        const double mx = fmax(fabs(pp), fabs(qq));
+        if (mx > 0.0 && isfinite(mx)) { const int e = ilogb(mx); pp = scalbn(pp, -e); qq = scalbn(qq, -e); }
+    }
+    bool b_ = false;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (s < cnt) {
+            const double e2 = ein[s] * ein[s];
+            const double np = D[s] * pp - e2 * qq;
+            qq = pp;
+            pp = np;
+            const double mi = qq / pp;
+            minv[s] = mi;
+            b_ |= !(mi > 0.0) || !isfinite(mi);
+        } else {
+            minv[s] = 0.0;
+        }
+    }
+    // chain ends: 1/M_{m-1} = q/p of the top prefix (lane 15), 1/M_{m+1} of lane 31
+    const double t_inv = __shfl_sync(FULL, p21, 15) / __shfl_sync(FULL, p11, 15);
+    const double b_inv = __shfl_sync(FULL, p21, 31) / __shfl_sync(FULL, p11, 31);
+    const double Mm = Dm - em1 * em1 * t_inv - em * em * b_inv;
+    minv_m = 1.0 / Mm;
+    b_ |= !(Mm > 0.0) || !isfinite(Mm);
+    bad = b_;
+}
+
+// ---------------------------------------------------------------- misc
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The element-per-lane split used by every line kernel: S = the smallest
+// supported slot count with 16 * S >= the longer chain of an nx-cell line.
+#define FFP_SLOT_LIST(X) X(1) X(2) X(3) X(4) X(6) X(8) X(11) X(16) X(22) X(32)
+
+inline int slots_for(int nx) {
+    if (nx > FFP_MAX_NX) return -1;
+    const int nbot = nx - 1 - (nx - 1) / 2;
+    const int need = (nbot + 15) / 16;
+    const int list[] = {1, 2, 3, 4, 6, 8, 11, 16, 22, 32};
+    for (int s : list)
+        if (s >= need) return s;
+    return -1;
+}
+
+// ---------------------------------------------------------------- workspace
+struct Ws {
+    // operator bands (FP64)
+    double *d, *cx, *cy, *cz;
+    // factors in storage precision: l1 (x-band of T), minv (1/M), l2 (y-band of P), l3 (z-band of A)
+    void *l1, *minv, *l2, *l3;
+    // combination preconditioner: ILU(0) 1/D and the x, y bands of A in storage precision
+    void *dinv, *lx, *ly;
+    // combination temporaries
+    double *c1, *c2;
+    // CG vectors
+    double *r, *z, *p, *q;
+    // apply scratch: 2 planes (one per level-3 half) of FP64
+    double *ascr;
+    // setup scratch, per half h: P bands ping-pong [h][pp][3], FP64 line factors of the
+    // current plane [h][2] (l1, minv), w/v/beta plane [h][2], correction to the twist plane [h][3]
+    double *sP[2][2][3];
+    double *sF[2][2];
+    double *sW[2][2];
+    double *sC[2][3];
+    // reductions
+    double *red;   // partial sums [kRedSlots]
+    double *scal;  // scalars [kScal]
+    int *flags;    // error flags [16]
+};
+
+constexpr int kRedBlocks = 1216;  // 8 x 152 SMs
+constexpr int kRedSlots = kRedBlocks * 4;
+constexpr int kScal = 64;
+
+// scalar slots
+enum {
+    SC_BB = 0,     // ||b||^2
+    SC_RR = 1,     // ||r||^2 (recursive)
+    SC_RHO = 2,    // (r, z)
+    SC_RHO_OLD = 3,
+    SC_PQ = 4,     // (p, A p)
+    SC_ALPHA = 5,
+    SC_BETA = 6,
+    SC_ZQ = 7,     // (z, q)  (flexible CG)
+    SC_TRR = 8,    // ||b - A x||^2
+};
+// flag slots
+enum { FL_BREAKDOWN = 0, FL_ARG = 1, FL_PQ = 2 };
+
+}  // namespace ffp

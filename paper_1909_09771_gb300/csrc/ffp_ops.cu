@@ -1,0 +1,390 @@
+// ffp_ops.cu -- operator assembly, SpMV and the FP64 CG vector kernels.
+//
+// Assembly (Sec. I Eq. (2), finite-volume reading): face coefficient
+// kappa_f * area / distance with kappa_f = 2 ka kb / (ka + kb); a Dirichlet
+// face at half a cell contributes 2 kappa * area / h to the diagonal; faces
+// are summed in the order x-, x+, y-, y+, z-, z+.
+// SpMV (Sec. II band storage): y_a = d_a x_a + sum of the six couplings.
+// Reductions are deterministic: a fixed grid, a fixed per-block tree and a
+// fixed-order final sum in finalize_kernel.
+#include "ffp_kernels.h"
+
+namespace ffp {
+
+constexpr int kThreads = 256;
+
+struct Geo {
+    int nx, ny, nz;
+    long long n;
+    int nxy;
+};
+
+__device__ __forceinline__ double harmonic(double ka, double kb) { return 2.0 * ka * kb / (ka + kb); }
+
+__global__ void __launch_bounds__(kThreads) assemble_kernel(Geo g, double ax, double ay, double az,
+                                                           const double *__restrict__ kappa,
+                                                           uchar4 bc03, uchar2 bc45, double *d,
+                                                           double *cx, double *cy, double *cz,
+                                                           int *flags) {
+    const unsigned char bc[6] = {bc03.x, bc03.y, bc03.z, bc03.w, bc45.x, bc45.y};
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(a % g.nx);
+        const int y = (int)((a / g.nx) % g.ny);
+        const int z = (int)(a / g.nxy);
+        const double ka = kappa[a];
+        if (!(ka > 0.0) || !isfinite(ka)) atomicOr(flags + FL_ARG, 1);
+        double diag = 0.0;
+        if (x > 0) diag += harmonic(ka, kappa[a - 1]) * ax;
+        else if (bc[0] == FFP_DIRICHLET) diag += 2.0 * ka * ax;
+        if (x + 1 < g.nx) { const double c = harmonic(ka, kappa[a + 1]) * ax; cx[a] = -c; diag += c; }
+        else { cx[a] = 0.0; if (bc[1] == FFP_DIRICHLET) diag += 2.0 * ka * ax; }
+        if (y > 0) diag += harmonic(ka, kappa[a - g.nx]) * ay;
+        else if (bc[2] == FFP_DIRICHLET) diag += 2.0 * ka * ay;
+        if (y + 1 < g.ny) { const double c = harmonic(ka, kappa[a + g.nx]) * ay; cy[a] = -c; diag += c; }
+        else { cy[a] = 0.0; if (bc[3] == FFP_DIRICHLET) diag += 2.0 * ka * ay; }
+        if (z > 0) diag += harmonic(ka, kappa[a - g.nxy]) * az;
+        else if (bc[4] == FFP_DIRICHLET) diag += 2.0 * ka * az;
+        if (z + 1 < g.nz) { const double c = harmonic(ka, kappa[a + g.nxy]) * az; cz[a] = -c; diag += c; }
+        else { cz[a] = 0.0; if (bc[5] == FFP_DIRICHLET) diag += 2.0 * ka * az; }
+        d[a] = diag;
+    }
+}
+
+__global__ void check_filter_kernel(long long n, const double *__restrict__ t, int *flags) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const double v = t[a];
+        if (!(v > 0.0) || !isfinite(v)) atomicOr(flags + FL_ARG, 1);
+    }
+}
+
+template <typename F>
+__global__ void convert_kernel(long long n, const double *__restrict__ s, F *o) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        o[a] = from_d<F>(s[a]);
+}
+
+template <typename F>
+__global__ void export_kernel(long long n, const F *__restrict__ s, double *o) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        o[a] = (double)to_r(s[a], typename Compute<F>::type());
+}
+
+// (A x)_a with the oracle's term order.
+__device__ __forceinline__ double stencil(const Geo &g, long long a, const double *__restrict__ d,
+                                          const double *__restrict__ cx,
+                                          const double *__restrict__ cy,
+                                          const double *__restrict__ cz,
+                                          const double *__restrict__ x) {
+    const int ix = (int)(a % g.nx);
+    const int iy = (int)((a / g.nx) % g.ny);
+    const int iz = (int)(a / g.nxy);
+    double s = d[a] * x[a];
+    if (ix > 0) s += cx[a - 1] * x[a - 1];
+    if (ix + 1 < g.nx) s += cx[a] * x[a + 1];
+    if (iy > 0) s += cy[a - g.nx] * x[a - g.nx];
+    if (iy + 1 < g.ny) s += cy[a] * x[a + g.nx];
+    if (iz > 0) s += cz[a - g.nxy] * x[a - g.nxy];
+    if (iz + 1 < g.nz) s += cz[a] * x[a + g.nxy];
+    return s;
+}
+
+__global__ void __launch_bounds__(kThreads) spmv_kernel(Geo g, const double *__restrict__ d,
+                                                       const double *__restrict__ cx,
+                                                       const double *__restrict__ cy,
+                                                       const double *__restrict__ cz,
+                                                       const double *__restrict__ x, double *y) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.n;
+         a += (long long)gridDim.x * blockDim.x)
+        y[a] = stencil(g, a, d, cx, cy, cz, x);
+}
+
+// w = r - A y
+__global__ void __launch_bounds__(kThreads) resid_vec_kernel(Geo g, const double *__restrict__ d,
+                                                            const double *__restrict__ cx,
+                                                            const double *__restrict__ cy,
+                                                            const double *__restrict__ cz,
+                                                            const double *__restrict__ r,
+                                                            const double *__restrict__ y,
+                                                            double *w) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.n;
+         a += (long long)gridDim.x * blockDim.x)
+        w[a] = r[a] - stencil(g, a, d, cx, cy, cz, y);
+}
+
+__global__ void __launch_bounds__(kThreads) add_kernel(long long n, double *z,
+                                                      const double *__restrict__ y) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        z[a] += y[a];
+}
+
+// Block sum of NV values per thread, written to red[blockIdx.x * NV + v], fixed order.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *red) {
+    __shared__ double sh[NV][kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) s += sh[k][w];
+            red[blockIdx.x * NV + k] = s;
+        }
+    }
+}
+
+// r = b - A x ; partials (r.r, b.b)
+__global__ void __launch_bounds__(kThreads) resid_kernel(Geo g, const double *__restrict__ d,
+                                                        const double *__restrict__ cx,
+                                                        const double *__restrict__ cy,
+                                                        const double *__restrict__ cz,
+                                                        const double *__restrict__ b,
+                                                        const double *__restrict__ x, double *r,
+                                                        double *red) {
+    double acc[2] = {0.0, 0.0};
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const double ba = b[a];
+        const double ra = ba - stencil(g, a, d, cx, cy, cz, x);
+        r[a] = ra;
+        acc[0] += ra * ra;
+        acc[1] += ba * ba;
+    }
+    block_sum<2>(acc, red);
+}
+
+// q = A p ; partial (p.q)
+__global__ void __launch_bounds__(kThreads) spmv_dot_kernel(Geo g, const double *__restrict__ d,
+                                                           const double *__restrict__ cx,
+                                                           const double *__restrict__ cy,
+                                                           const double *__restrict__ cz,
+                                                           const double *__restrict__ p, double *q,
+                                                           double *red) {
+    double acc[1] = {0.0};
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const double qa = stencil(g, a, d, cx, cy, cz, p);
+        q[a] = qa;
+        acc[0] += p[a] * qa;
+    }
+    block_sum<1>(acc, red);
+}
+
+// x += alpha p ; r -= alpha q ; partial (r.r)
+__global__ void __launch_bounds__(kThreads) update_xr_kernel(long long n,
+                                                            const double *__restrict__ scal,
+                                                            const double *__restrict__ p,
+                                                            const double *__restrict__ q, double *x,
+                                                            double *r, double *red) {
+    const double alpha = scal[SC_ALPHA];
+    double acc[1] = {0.0};
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        x[a] += alpha * p[a];
+        const double ra = r[a] - alpha * q[a];
+        r[a] = ra;
+        acc[0] += ra * ra;
+    }
+    block_sum<1>(acc, red);
+}
+
+// partials (r.z, z.q)
+__global__ void __launch_bounds__(kThreads) dot_rz_kernel(long long n, const double *__restrict__ r,
+                                                         const double *__restrict__ z,
+                                                         const double *__restrict__ q,
+                                                         double *red) {
+    double acc[2] = {0.0, 0.0};
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const double za = z[a];
+        acc[0] += r[a] * za;
+        acc[1] += za * q[a];
+    }
+    block_sum<2>(acc, red);
+}
+
+// p = z + beta p  (p = z when the direction is (re)started)
+__global__ void __launch_bounds__(kThreads) update_p_kernel(long long n,
+                                                           const double *__restrict__ scal,
+                                                           const double *__restrict__ z, double *p,
+                                                           int fresh) {
+    const double beta = scal[SC_BETA];
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        p[a] = fresh ? z[a] : z[a] + beta * p[a];
+}
+
+// Sum of red[i*stride + k], i < nblk, by one warp in a fixed order (lane-strided
+// partial sums, then a fixed shuffle tree); every lane gets the result.
+__device__ __forceinline__ double warp_fold(const double *__restrict__ red, int nblk, int stride,
+                                            int k) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < nblk; i += 32) s += red[i * stride + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Fold the partial sums and update the CG scalars (one warp).
+__global__ void finalize_kernel(int mode, int nblk, int fresh, int flexible,
+                                const double *__restrict__ red, double *scal, int *flags) {
+    if (mode == FIN_RESID) {
+        const double rr = warp_fold(red, nblk, 2, 0);
+        const double bb = warp_fold(red, nblk, 2, 1);
+        if (threadIdx.x == 0) { scal[SC_TRR] = rr; scal[SC_RR] = rr; scal[SC_BB] = bb; }
+    } else if (mode == FIN_PQ) {
+        const double pq = warp_fold(red, nblk, 1, 0);
+        if (threadIdx.x == 0) {
+            scal[SC_PQ] = pq;
+            if (!(pq > 0.0) || !isfinite(pq)) flags[FL_PQ] = 1;
+            scal[SC_ALPHA] = scal[SC_RHO] / pq;
+        }
+    } else if (mode == FIN_RR) {
+        const double rr = warp_fold(red, nblk, 1, 0);
+        if (threadIdx.x == 0) scal[SC_RR] = rr;
+    } else {
+        const double rz = warp_fold(red, nblk, 2, 0);
+        const double zq = warp_fold(red, nblk, 2, 1);
+        if (threadIdx.x == 0) {
+            double beta = 0.0;
+            if (!fresh) {
+                if (flexible) beta = -scal[SC_ALPHA] * zq / scal[SC_RHO];  // (z, r_new - r_old) / rho
+                else beta = rz / scal[SC_RHO];
+            }
+            scal[SC_BETA] = beta;
+            scal[SC_ZQ] = zq;
+            scal[SC_RHO_OLD] = scal[SC_RHO];
+            scal[SC_RHO] = rz;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static Geo geo(const KernelCtx &c) {
+    Geo g;
+    g.nx = c.nx; g.ny = c.ny; g.nz = c.nz; g.n = c.n; g.nxy = c.nx * c.ny;
+    return g;
+}
+
+static int grid_for(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    if (b > kRedBlocks) b = kRedBlocks;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_assemble(const KernelCtx &c, const double *kappa, const unsigned char bc[6],
+                            cudaStream_t st) {
+    const double hx = c.lx / c.nx, hy = c.ly / c.ny, hz = c.lz / c.nz;
+    const double ax = hy * hz / hx, ay = hx * hz / hy, az = hx * hy / hz;
+    uchar4 b03 = make_uchar4(bc[0], bc[1], bc[2], bc[3]);
+    uchar2 b45 = make_uchar2(bc[4], bc[5]);
+    assemble_kernel<<<grid_for(c.n), kThreads, 0, st>>>(geo(c), ax, ay, az, kappa, b03, b45,
+                                                        c.ws.d, c.ws.cx, c.ws.cy, c.ws.cz,
+                                                        c.ws.flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_filter(const KernelCtx &c, const double *t, cudaStream_t st) {
+    check_filter_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, t, c.ws.flags);
+    return cudaGetLastError();
+}
+
+template <typename F>
+static void convert_all(const KernelCtx &c, cudaStream_t st) {
+    convert_kernel<F><<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.ws.cz, (F *)c.ws.l3);
+    if (c.precond == FFP_PRECOND_COMBO) {
+        convert_kernel<F><<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.ws.cx, (F *)c.ws.lx);
+        convert_kernel<F><<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.ws.cy, (F *)c.ws.ly);
+    }
+}
+
+cudaError_t launch_convert_bands(const KernelCtx &c, cudaStream_t st) {
+    switch (c.prec) {
+        case FFP_FP64: convert_all<double>(c, st); break;
+        case FFP_FP32: convert_all<float>(c, st); break;
+        default: convert_all<__nv_bfloat16>(c, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(const KernelCtx &c, const void *src, double *dst, cudaStream_t st) {
+    switch (c.prec) {
+        case FFP_FP64:
+            export_kernel<double><<<grid_for(c.n), kThreads, 0, st>>>(c.n, (const double *)src, dst);
+            break;
+        case FFP_FP32:
+            export_kernel<float><<<grid_for(c.n), kThreads, 0, st>>>(c.n, (const float *)src, dst);
+            break;
+        default:
+            export_kernel<__nv_bfloat16><<<grid_for(c.n), kThreads, 0, st>>>(
+                c.n, (const __nv_bfloat16 *)src, dst);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(const KernelCtx &c, const double *x, double *y, cudaStream_t st) {
+    spmv_kernel<<<grid_for(c.n), kThreads, 0, st>>>(geo(c), c.ws.d, c.ws.cx, c.ws.cy, c.ws.cz, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_vec(const KernelCtx &c, const double *r, const double *y, double *w,
+                             cudaStream_t st) {
+    resid_vec_kernel<<<grid_for(c.n), kThreads, 0, st>>>(geo(c), c.ws.d, c.ws.cx, c.ws.cy, c.ws.cz,
+                                                         r, y, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add(const KernelCtx &c, double *z, const double *y, cudaStream_t st) {
+    add_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, z, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid(const KernelCtx &c, const double *b, const double *x, cudaStream_t st) {
+    resid_kernel<<<grid_for(c.n), kThreads, 0, st>>>(geo(c), c.ws.d, c.ws.cx, c.ws.cy, c.ws.cz, b, x,
+                                                     c.ws.r, c.ws.red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_dot(const KernelCtx &c, cudaStream_t st) {
+    spmv_dot_kernel<<<grid_for(c.n), kThreads, 0, st>>>(geo(c), c.ws.d, c.ws.cx, c.ws.cy, c.ws.cz,
+                                                        c.ws.p, c.ws.q, c.ws.red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_xr(const KernelCtx &c, double *x, cudaStream_t st) {
+    update_xr_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.ws.scal, c.ws.p, c.ws.q, x, c.ws.r,
+                                                         c.ws.red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_rz(const KernelCtx &c, cudaStream_t st) {
+    dot_rz_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.ws.r, c.ws.z, c.ws.q, c.ws.red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_p(const KernelCtx &c, int fresh, cudaStream_t st) {
+    update_p_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.ws.scal, c.ws.z, c.ws.p, fresh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const KernelCtx &c, int mode, int fresh, int flexible, cudaStream_t st) {
+    finalize_kernel<<<1, 32, 0, st>>>(mode, grid_for(c.n), fresh, flexible, c.ws.red, c.ws.scal,
+                                      c.ws.flags);
+    return cudaGetLastError();
+}
+
+}  // namespace ffp

@@ -1,0 +1,376 @@
+// ffp_setup.cu -- construction of the nested twisted filtering preconditioner
+// (Sec. II-A), FP64, stored in the requested precision.
+//
+// Level 3 (planes), twisted at mz = floor((nz-1)/2):
+//   phase 0 (2 CTAs, one per half): P_0 = Dhat_0 (top) / P_{nz-1} = Dhat_{nz-1}
+//     (bottom); for each plane of the half, in elimination order:
+//       (a) level-2 factorization of P_i (lines, below),
+//       (b) w = C t_dst, v = B_{P,i}^{-1} w by the nested plane solve (reading R1),
+//           beta = v ./ w,
+//       (c) the Schur term C (2 beta - beta P_i beta) C of the next plane dst of
+//           the chain: P_dst = Dhat_dst - C X C, or, for the last plane of the
+//           half, saved for the twist plane.
+//   phase 1 (1 CTA): P_mz = Dhat_mz - (term from mz-1) - (term from mz+1), then
+//     its level-2 factorization.
+// Level 2 (lines of P_i), twisted at my = floor((ny-1)/2), warps 0 and 1:
+//   T_0 = Dbar_0 / T_{ny-1} = Dbar_{ny-1}; T_k = Dbar_k - p X p with
+//   X = 2 beta - beta T_prev beta, beta = (T_prev^{-1} w) ./ w, w = p .* t_k,
+//   p = y-band of P_i between the two lines; the twist line takes both terms.
+// Level 1: twisted pivots M of every T_k (exact), see twisted_pivots().
+// Stored: l1 = x-band of T_k, minv = 1/M, l2 = y-band of P_i (l3 = z-band of A
+// is converted separately).
+#pragma once
+#include "ffp_plane.cuh"
+#include "ffp_kernels.h"
+
+namespace ffp {
+
+struct SetupArgs {
+    int nx, ny, nz;
+    int prec;  // storage precision of l1, minv, l2
+    const double *d, *cx, *cy, *cz;
+    const double *t;  // filter, NULL = rowsum
+    void *l1, *minv, *l2;
+    Ws ws;
+};
+
+// Store one factor entry in the storage precision.
+__device__ __forceinline__ void put_factor(void *base, long idx, double v, int prec) {
+    if (prec == FFP_FP64) static_cast<double *>(base)[idx] = v;
+    else if (prec == FFP_FP32) static_cast<float *>(base)[idx] = (float)v;
+    else static_cast<__nv_bfloat16 *>(base)[idx] = __double2bfloat16(v);
+}
+
+struct SetupPol {
+    const double *W;
+    double *V;
+    int nx;
+    __device__ __forceinline__ double rhs(int k, int a) const { return W[(long)k * nx + a]; }
+    __device__ __forceinline__ void put_w(int k, int a, double w) const { V[(long)k * nx + a] = w; }
+    __device__ __forceinline__ double get_w(int k, int a) const { return V[(long)k * nx + a]; }
+    __device__ __forceinline__ void put_out(int k, int a, double u) const { V[(long)k * nx + a] = u; }
+};
+
+// State of the previous line T_prev as seen by this lane.
+template <int S>
+struct LineState {
+    LineFactor<S, double> f;
+    double Td[S], To[S], Tdm, Tom;
+};
+
+// beta of the level-2 Schur term from T_prev onto the line with coupling p
+// (global, this line's cells) and filter tl (or NULL): returns the terms
+// cd = p X p (diagonal) and co = p X p (x-band) per slot and for the twist cell.
+template <int S>
+__device__ __forceinline__ void line_schur(const LineMap &L, int nx, int lane, int cnt,
+                                           const LineState<S> &st, const double *p,
+                                           const double *tl, double *SB, double *SP,
+                                           double (&cd)[S], double (&co)[S], double &cdm,
+                                           double &com) {
+    double w[S], wm, pa[S], pm;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (s < cnt) {
+            const int a = slot_cell<S>(L, lane, s);
+            pa[s] = p[a];
+            w[s] = pa[s] * (tl ? tl[a] : 1.0);
+        } else {
+            pa[s] = 0.0; w[s] = 0.0;
+        }
+    }
+    pm = p[L.m];
+    wm = pm * (tl ? tl[L.m] : 1.0);
+    double v[S], vm;
+    twisted_solve<S, double>(st.f, cnt, lane, w, wm, v, vm);  // v = T_prev^{-1} w
+    double be[S], bem;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (s < cnt) {
+            be[s] = (fabs(w[s]) < 1e-300) ? 1.0 / st.Td[s] : v[s] / w[s];
+            const int a = slot_cell<S>(L, lane, s);
+            SB[a] = be[s];
+            SP[a] = pa[s];
+        } else {
+            be[s] = 0.0;
+        }
+    }
+    bem = (fabs(wm) < 1e-300) ? 1.0 / st.Tdm : vm / wm;
+    if (lane == 0) { SB[L.m] = bem; SP[L.m] = pm; }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (s < cnt) {
+            const int a = slot_cell<S>(L, lane, s);
+            const double xd = 2.0 * be[s] - be[s] * st.Td[s] * be[s];
+            cd[s] = pa[s] * xd * pa[s];
+            if (a + 1 < nx) {
+                const double xo = -be[s] * st.To[s] * SB[a + 1];
+                co[s] = pa[s] * xo * SP[a + 1];
+            } else {
+                co[s] = 0.0;
+            }
+        } else {
+            cd[s] = 0.0; co[s] = 0.0;
+        }
+    }
+    {
+        const double xd = 2.0 * bem - bem * st.Tdm * bem;
+        cdm = pm * xd * pm;
+        if (L.m + 1 < nx) {
+            const double xo = -bem * st.Tom * SB[L.m + 1];
+            com = pm * xo * SP[L.m + 1];
+        } else {
+            com = 0.0;
+        }
+    }
+    __syncwarp();
+}
+
+// Twisted pivots of T = tridiag(To, Td, To) of one line -> line state.
+template <int S>
+__device__ __forceinline__ void factor_line(const LineMap &L, int lane, int cnt,
+                                            const double (&Td)[S], const double (&To)[S],
+                                            double Tdm, double Tom, double *SO,
+                                            LineState<S> &st, int *flags) {
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+        if (s < cnt) SO[slot_cell<S>(L, lane, s)] = To[s];
+    if (lane == 0) SO[L.m] = Tom;
+    __syncwarp();
+    double ein[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (s < cnt) {
+            const int a = slot_cell<S>(L, lane, s);
+            const double e_lo = (a > 0) ? SO[a - 1] : 0.0;
+            const double e_hi = To[s];
+            if (lane < 16) { st.f.ein[s] = e_lo; st.f.eout[s] = e_hi; }
+            else { st.f.ein[s] = e_hi; st.f.eout[s] = e_lo; }
+            ein[s] = st.f.ein[s];
+        } else {
+            st.f.ein[s] = 0.0; st.f.eout[s] = 0.0; ein[s] = 0.0;
+        }
+        st.Td[s] = Td[s];
+        st.To[s] = To[s];
+    }
+    st.f.em1 = (L.m > 0) ? SO[L.m - 1] : 0.0;
+    st.f.em = Tom;
+    st.Tdm = Tdm;
+    st.Tom = Tom;
+    bool bad = false;
+    twisted_pivots<S>(cnt, lane, Td, ein, Tdm, st.f.em1, st.f.em, st.f.minv, st.f.minv_m, bad);
+    if (bad) atomicOr(flags + FL_BREAKDOWN, 1);
+    __syncwarp();
+}
+
+template <int S>
+__device__ __forceinline__ void store_line(const LineMap &L, int lane, int cnt, int nx, int k,
+                                           const LineState<S> &st, double *l1d, double *mid,
+                                           void *l1f, void *mif, long goff, int prec) {
+    const long o = (long)k * nx;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+        if (s < cnt) {
+            const int a = slot_cell<S>(L, lane, s);
+            l1d[o + a] = st.To[s];
+            mid[o + a] = st.f.minv[s];
+            put_factor(l1f, goff + o + a, st.To[s], prec);
+            put_factor(mif, goff + o + a, st.f.minv[s], prec);
+        }
+    if (lane == 0) {
+        l1d[o + L.m] = st.Tom;
+        mid[o + L.m] = st.f.minv_m;
+        put_factor(l1f, goff + o + L.m, st.Tom, prec);
+        put_factor(mif, goff + o + L.m, st.f.minv_m, prec);
+    }
+}
+
+// Level-2 factorization of one plane (warps 0 and 1).  Pd/Px/Py: bands of P
+// (plane slice, FP64); tp: filter on the plane or NULL; outputs the FP64 line
+// factors (l1d, mid) used by the nested plane solve and the stored factors.
+template <int S>
+__device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
+                             const double *Px, const double *Py, const double *tp, double *l1d,
+                             double *mid, void *l1f, void *mif, long goff, int prec, double *lbuf,
+                             double *meet, int wid, int lane, int cnt, int *flags) {
+    const int my = (ny - 1) / 2;
+    const int nl = (wid == 0) ? my : ny - 1 - my;
+    double *SB = lbuf + wid * 3 * nx, *SP = SB + nx, *SO = SP + nx;
+    LineState<S> st;
+    double Td[S], To[S], Tdm, Tom, cd[S], co[S], cdm, com;
+    for (int t = 0; t < nl; ++t) {
+        const int k = (wid == 0) ? t : ny - 1 - t;
+        const long o = (long)k * nx;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (s < cnt) {
+                const int a = slot_cell<S>(L, lane, s);
+                Td[s] = Pd[o + a];
+                To[s] = Px[o + a];
+            } else {
+                Td[s] = 1.0; To[s] = 0.0;
+            }
+        }
+        Tdm = Pd[o + L.m];
+        Tom = Px[o + L.m];
+        if (t > 0) {
+            const int kc = (wid == 0) ? k - 1 : k;
+            line_schur<S>(L, nx, lane, cnt, st, Py + (long)kc * nx, tp ? tp + o : nullptr, SB, SP,
+                          cd, co, cdm, com);
+#pragma unroll
+            for (int s = 0; s < S; ++s) { Td[s] -= cd[s]; To[s] -= co[s]; }
+            Tdm -= cdm;
+            Tom -= com;
+        }
+        factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags);
+        store_line<S>(L, lane, cnt, nx, k, st, l1d, mid, l1f, mif, goff, prec);
+    }
+    // twist line: Schur terms from both halves
+    {
+        const long o = (long)my * nx;
+        const int kc = (wid == 0) ? my - 1 : my;
+        if (nl > 0) {
+            line_schur<S>(L, nx, lane, cnt, st, Py + (long)kc * nx, tp ? tp + o : nullptr, SB, SP,
+                          cd, co, cdm, com);
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) { cd[s] = 0.0; co[s] = 0.0; }
+            cdm = 0.0; com = 0.0;
+        }
+        double *MD = meet + wid * 2 * nx, *MO = MD + nx;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (s < cnt) {
+                const int a = slot_cell<S>(L, lane, s);
+                MD[a] = cd[s];
+                MO[a] = co[s];
+            }
+        if (lane == 0) { MD[L.m] = cdm; MO[L.m] = com; }
+        named_barrier(2, 64);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (s < cnt) {
+                const int a = slot_cell<S>(L, lane, s);
+                Td[s] = Pd[o + a] - meet[a] - meet[2 * nx + a];
+                To[s] = Px[o + a] - meet[nx + a] - meet[3 * nx + a];
+            } else {
+                Td[s] = 1.0; To[s] = 0.0;
+            }
+        }
+        Tdm = Pd[o + L.m] - meet[L.m] - meet[2 * nx + L.m];
+        Tom = Px[o + L.m] - meet[nx + L.m] - meet[3 * nx + L.m];
+        factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags);
+        if (wid == 0) store_line<S>(L, lane, cnt, nx, my, st, l1d, mid, l1f, mif, goff, prec);
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) setup_kernel(SetupArgs A, int phase) {
+    extern __shared__ __align__(16) double sm[];
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const long nxy = (long)nx * ny;
+    double *gbuf = sm;                 // plane solve exchange [2][2][nx]
+    double *lbuf = sm + 4 * nx;        // level-2 line buffers [2 warps][3][nx]
+    double *meet = sm + 10 * nx;       // level-2 twist exchange [2 warps][2][nx]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const LineMap L(nx);
+    const int cnt = lane_count<S>(L, lane);
+    const int mz = (nz - 1) / 2;
+    int *flags = A.ws.flags;
+    if (phase == 0) {
+        const int h = blockIdx.x;
+        const int nl3 = (h == 0) ? mz : nz - 1 - mz;
+        double *l1d = A.ws.sF[h][0], *mid = A.ws.sF[h][1];
+        double *W = A.ws.sW[h][0], *V = A.ws.sW[h][1];
+        for (int t = 0; t < nl3; ++t) {
+            const int i = (h == 0) ? t : nz - 1 - t;
+            const double *Pd, *Px, *Py;
+            if (t == 0) {
+                Pd = A.d + i * nxy; Px = A.cx + i * nxy; Py = A.cy + i * nxy;
+            } else {
+                Pd = A.ws.sP[h][t & 1][0]; Px = A.ws.sP[h][t & 1][1]; Py = A.ws.sP[h][t & 1][2];
+            }
+            for (long e = tid; e < nxy; e += blockDim.x) put_factor(A.l2, i * nxy + e, Py[e], A.prec);
+            if (wid < 2)
+                level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + i * nxy : nullptr, l1d, mid,
+                                A.l1, A.minv, i * nxy, A.prec, lbuf, meet, wid, lane, cnt, flags);
+            const int dst = (t == nl3 - 1) ? mz : ((h == 0) ? i + 1 : i - 1);
+            const int ic = (i < dst) ? i : dst;
+            const double *C = A.cz + ic * nxy;
+            for (long e = tid; e < nxy; e += blockDim.x)
+                W[e] = C[e] * (A.t ? A.t[dst * nxy + e] : 1.0);
+            __syncthreads();
+            if (wid < 2) {
+                SetupPol pol{W, V, nx};
+                plane_solve<S, false, double, double>(L, nx, ny, l1d, mid, Py, pol, gbuf, wid, lane,
+                                                      cnt);
+            }
+            __syncthreads();
+            for (long e = tid; e < nxy; e += blockDim.x)
+                V[e] = (fabs(W[e]) < 1e-300) ? 1.0 / Pd[e] : V[e] / W[e];
+            __syncthreads();
+            const bool to_mid = (dst == mz);
+            double *od = to_mid ? A.ws.sC[h][0] : A.ws.sP[h][(t + 1) & 1][0];
+            double *ox = to_mid ? A.ws.sC[h][1] : A.ws.sP[h][(t + 1) & 1][1];
+            double *oy = to_mid ? A.ws.sC[h][2] : A.ws.sP[h][(t + 1) & 1][2];
+            for (long e = tid; e < nxy; e += blockDim.x) {
+                const int ix = (int)(e % nx), iy = (int)(e / nx);
+                const double be = V[e];
+                const double xd = 2.0 * be - be * Pd[e] * be;
+                const double cd = C[e] * xd * C[e];
+                double cxo = 0.0, cyo = 0.0;
+                if (ix + 1 < nx) {
+                    const double xo = -be * Px[e] * V[e + 1];
+                    cxo = C[e] * xo * C[e + 1];
+                }
+                if (iy + 1 < ny) {
+                    const double xo = -be * Py[e] * V[e + nx];
+                    cyo = C[e] * xo * C[e + nx];
+                }
+                if (to_mid) {
+                    od[e] = cd; ox[e] = cxo; oy[e] = cyo;
+                } else {
+                    const long g = (long)dst * nxy + e;
+                    od[e] = A.d[g] - cd;
+                    ox[e] = A.cx[g] - cxo;
+                    oy[e] = A.cy[g] - cyo;
+                }
+            }
+            __syncthreads();
+        }
+    } else {
+        double *Pd = A.ws.sP[0][0][0], *Px = A.ws.sP[0][0][1], *Py = A.ws.sP[0][0][2];
+        const long g0 = (long)mz * nxy;
+        for (long e = tid; e < nxy; e += blockDim.x) {
+            double vd = A.d[g0 + e], vx = A.cx[g0 + e], vy = A.cy[g0 + e];
+            if (mz > 0) { vd -= A.ws.sC[0][0][e]; vx -= A.ws.sC[0][1][e]; vy -= A.ws.sC[0][2][e]; }
+            if (mz < nz - 1) { vd -= A.ws.sC[1][0][e]; vx -= A.ws.sC[1][1][e]; vy -= A.ws.sC[1][2][e]; }
+            Pd[e] = vd; Px[e] = vx; Py[e] = vy;
+            put_factor(A.l2, g0 + e, vy, A.prec);
+        }
+        __syncthreads();
+        if (wid < 2)
+            level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + g0 : nullptr, A.ws.sF[0][0],
+                            A.ws.sF[0][1], A.l1, A.minv, g0, A.prec, lbuf, meet, wid, lane, cnt,
+                            flags);
+    }
+}
+
+template <int S>
+cudaError_t setup_for_slots(const KernelCtx &c, const double *t, cudaStream_t st) {
+    SetupArgs a;
+    a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.prec = c.prec;
+    a.d = c.ws.d; a.cx = c.ws.cx; a.cy = c.ws.cy; a.cz = c.ws.cz;
+    a.t = t;
+    a.l1 = c.ws.l1; a.minv = c.ws.minv; a.l2 = c.ws.l2;
+    a.ws = c.ws;
+    const size_t smem = sizeof(double) * 14 * (size_t)a.nx;
+    cudaError_t e = cudaFuncSetAttribute(setup_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (a.nz > 1) setup_kernel<S><<<2, 256, smem, st>>>(a, 0);
+    setup_kernel<S><<<1, 256, smem, st>>>(a, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace ffp

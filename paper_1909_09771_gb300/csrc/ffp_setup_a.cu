@@ -1,0 +1,9 @@
+// Explicit instantiations of the setup kernels for a subset of the line
+// slot counts (split across TUs so the build compiles them in parallel).
+#include "ffp_setup.cuh"
+
+namespace ffp {
+#define X(SS) template cudaError_t setup_for_slots<SS>(const KernelCtx &, const double *, cudaStream_t);
+X(1) X(2) X(3) X(4) X(6)
+#undef X
+}  // namespace ffp

@@ -1,0 +1,211 @@
+"""Thin ctypes binding of libffp.so (C ABI in include/ffp.h).
+
+Argument marshalling only: every step of setup, apply, SpMV and the CG solve
+runs in the library's CUDA kernels.  PyTorch provides the device memory (the
+workspace and vectors) and the current CUDA stream.  There is no CPU fallback:
+if libffp.so is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffp.so")
+HEADER = os.path.join(_HERE, "..", "include", "ffp.h")
+
+FFP_OK = 0
+FFP_ERR_ARG = -1
+FFP_ERR_CUDA = -2
+FFP_ERR_BREAKDOWN = -3
+FFP_ERR_NOT_CONVERGED = -4
+FFP_ERR_UNSUPPORTED = -6
+FFP_MAX_NX = 1024
+
+FFP_DIRICHLET, FFP_NEUMANN = 0, 1
+FFP_FILTER_ROWSUM, FFP_FILTER_USER = 0, 1
+FFP_FP64, FFP_FP32, FFP_BF16 = 0, 1, 2
+FFP_PRECOND_NTD, FFP_PRECOND_COMBO = 0, 1
+PRECISIONS = {"fp64": FFP_FP64, "fp32": FFP_FP32, "bf16": FFP_BF16}
+PRECONDS = {"ntd": FFP_PRECOND_NTD, "combo": FFP_PRECOND_COMBO}
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("face", ctypes.c_ubyte * 6)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double), ("solve_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FFPError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+
+
+_lib = None
+
+
+def declared_functions():
+    """Names of the functions include/ffp.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ffp_[a-z_0-9]+)\s*\(", txt)))
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, P = ctypes.c_void_p, ctypes.POINTER
+    lib.ffp_workspace_bytes.argtypes = [P(Grid), ctypes.c_int]
+    lib.ffp_workspace_bytes.restype = ctypes.c_size_t
+    lib.ffp_setup.argtypes = [P(Grid), vp, P(BC), ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
+                              vp, ctypes.c_size_t, vp, P(vp)]
+    lib.ffp_spmv.argtypes = [vp, vp, vp, vp]
+    lib.ffp_apply.argtypes = [vp, vp, vp, vp]
+    lib.ffp_pcg_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, P(Stats), vp]
+    lib.ffp_export.argtypes = [vp] * 10
+    lib.ffp_destroy.argtypes = [vp]
+    lib.ffp_destroy.restype = None
+    lib.ffp_strerror.argtypes = [ctypes.c_int]
+    lib.ffp_strerror.restype = ctypes.c_char_p
+    for f in (lib.ffp_setup, lib.ffp_spmv, lib.ffp_apply, lib.ffp_pcg_solve, lib.ffp_export):
+        f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def strerror(status):
+    try:
+        return load().ffp_strerror(int(status)).decode()
+    except Exception:  # pragma: no cover - only when the library is missing
+        return "unknown"
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _grid(grid, lengths):
+    nx, ny, nz = (int(v) for v in grid)
+    lx, ly, lz = (float(v) for v in lengths)
+    return Grid(nx, ny, nz, lx, ly, lz)
+
+
+def workspace_bytes(grid, precision="fp64", lengths=(1.0, 1.0, 1.0)):
+    g = _grid(grid, lengths)
+    return int(load().ffp_workspace_bytes(ctypes.byref(g), PRECISIONS[precision]))
+
+
+def _dev_vec(x, n, name):
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64):
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if x.numel() != n or not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with {n} entries")
+    return x
+
+
+class Preconditioner:
+    """Operator A (assembled from kappa) and its preconditioner B on the
+    current CUDA device: precond "ntd" (B_NTD, Sec. II) or "combo" (B_c with the
+    ILU(0) smoother, Sec. III).  The workspace is a torch uint8 tensor kept by
+    this object; the library only points into it."""
+
+    def __init__(self, grid, kappa, bc, precision="fp64", t=None, lengths=(1.0, 1.0, 1.0),
+                 stream=None, precond="ntd"):
+        lib = load()
+        self.grid = tuple(int(v) for v in grid)
+        self.n = self.grid[0] * self.grid[1] * self.grid[2]
+        self.precision = precision
+        self.precond = precond
+        g = _grid(self.grid, lengths)
+        nbytes = lib.ffp_workspace_bytes(ctypes.byref(g), PRECISIONS[precision])
+        if nbytes == 0:
+            raise FFPError(FFP_ERR_ARG, "ffp_workspace_bytes")
+        dev = kappa.device
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        kappa = _dev_vec(kappa, self.n, "kappa")
+        if t is not None:
+            t = _dev_vec(t, self.n, "t")
+        self._keep = (kappa, t)
+        b = BC((ctypes.c_ubyte * 6)(*[int(v) for v in bc]))
+        h = ctypes.c_void_p()
+        st = lib.ffp_setup(ctypes.byref(g), _ptr(kappa), ctypes.byref(b),
+                           FFP_FILTER_USER if t is not None else FFP_FILTER_ROWSUM, _ptr(t),
+                           PRECISIONS[precision], PRECONDS[precond], _ptr(self.workspace),
+                           ctypes.c_size_t(nbytes),
+                           _stream(stream), ctypes.byref(h))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_setup")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ffp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spmv(self, x, y=None, stream=None):
+        x = _dev_vec(x, self.n, "x")
+        y = torch.empty_like(x) if y is None else _dev_vec(y, self.n, "y")
+        st = load().ffp_spmv(self._h, _ptr(x), _ptr(y), _stream(stream))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_spmv")
+        return y
+
+    def apply(self, r, z=None, stream=None):
+        r = _dev_vec(r, self.n, "r")
+        z = torch.empty_like(r) if z is None else _dev_vec(z, self.n, "z")
+        st = load().ffp_apply(self._h, _ptr(r), _ptr(z), _stream(stream))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_apply")
+        return z
+
+    def solve(self, b, x=None, rtol=1e-8, maxit=200, stream=None, check=True):
+        """PCG / flexible CG; returns (x, stats dict).  x (if given) is x0 and is
+        overwritten with the solution."""
+        b = _dev_vec(b, self.n, "b")
+        x = torch.zeros_like(b) if x is None else _dev_vec(x, self.n, "x")
+        s = Stats()
+        st = load().ffp_pcg_solve(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit),
+                                  ctypes.byref(s), _stream(stream))
+        if check and st not in (FFP_OK,):
+            raise FFPError(st, "ffp_pcg_solve")
+        return x, s.as_dict()
+
+    def export(self, stream=None):
+        """Stored operator bands and factors as FP64 device tensors."""
+        names = ["d", "cx", "cy", "cz", "l2", "l1", "minv", "dinv"]
+        out = {k: torch.empty(self.n, dtype=torch.float64, device=self.workspace.device)
+               for k in names}
+        st = load().ffp_export(self._h, *[_ptr(out[k]) for k in names], _stream(stream))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_export")
+        return out

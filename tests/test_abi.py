@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every function include/ffp.h
+declares; its host-only entry points behave without a GPU (no compute)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1909_09771_gb300 import build as B
+from paper_1909_09771_gb300 import ffp
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ffp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return ffp.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = ffp.declared_functions()
+    assert {"ffp_setup", "ffp_apply", "ffp_pcg_solve", "ffp_spmv", "ffp_workspace_bytes",
+            "ffp_destroy", "ffp_strerror", "ffp_export"} <= set(names)
+    raw = ctypes.CDLL(ffp.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), f"{n} declared in include/ffp.h but not exported"
+
+
+def test_header_constants_match_binding():
+    txt = open(HDR).read()
+    defs = dict(re.findall(r"#define\s+(FFP_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", txt))
+    for k, v in defs.items():
+        if hasattr(ffp, k):
+            assert getattr(ffp, k) == int(v), k
+
+
+def test_workspace_bytes_host_only(lib):
+    assert ffp.workspace_bytes((32, 32, 32), "fp64") > 32 ** 3 * 8 * 12
+    assert ffp.workspace_bytes((32, 32, 32), "fp32") < ffp.workspace_bytes((32, 32, 32), "fp64")
+    g = ffp.Grid(0, 4, 4, 1, 1, 1)
+    assert lib.ffp_workspace_bytes(ctypes.byref(g), 0) == 0
+    g = ffp.Grid(ffp.FFP_MAX_NX + 1, 2, 2, 1, 1, 1)
+    assert lib.ffp_workspace_bytes(ctypes.byref(g), 0) == 0
+    g = ffp.Grid(4, 4, 4, 1, 1, 1)
+    assert lib.ffp_workspace_bytes(ctypes.byref(g), 7) == 0
+
+
+def test_strerror_and_null_args(lib):
+    assert lib.ffp_strerror(0) == b"ok"
+    assert b"breakdown" in lib.ffp_strerror(ffp.FFP_ERR_BREAKDOWN)
+    # argument checks happen before any CUDA call
+    assert lib.ffp_apply(None, None, None, None) == ffp.FFP_ERR_ARG
+    assert lib.ffp_spmv(None, None, None, None) == ffp.FFP_ERR_ARG
+    h = ctypes.c_void_p()
+    g = ffp.Grid(4, 4, 4, 1, 1, 1)
+    assert lib.ffp_setup(ctypes.byref(g), None, None, 0, None, 0, 0, None, 0, None,
+                         ctypes.byref(h)) == ffp.FFP_ERR_ARG

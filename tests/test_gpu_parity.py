@@ -1,0 +1,293 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU
+oracle on the same seeded inputs.  Tolerances:
+  assembly / SpMV      1e-14 relative per entry (sum of |terms| for SpMV): the
+                       only difference is FMA contraction (one rounding per term)
+  setup factors, FP64  1e-10 relative per entry: beta = (T^{-1} w) ./ w inherits
+                       cond(T) of nearly singular Neumann lines, and the GPU
+                       evaluates the pivot continued fraction and the solves by
+                       scans (another rounding order) along the chains
+  apply kernel, FP64   1e-12 relative 2-norm against the oracle applying the
+                       GPU's own exported factors (isolates the apply's rounding)
+  setup + apply, FP64  1e-10 relative 2-norm (the setup's conditioning above)
+  apply, FP32 factors  1e-5 relative 2-norm (FP32 storage and arithmetic)
+  PCG, FP64            iterations equal +-1, solution 1e-7 relative, both true
+                       residuals below rtol
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as o
+from paper_1909_09771_gb300 import build as B
+from paper_1909_09771_gb300 import ffp
+from paper_1909_09771_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    ffp.load()
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def relerr(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def make(grid, seed, precision="fp64", contrast=3, bc=I.BC_Z_DIRICHLET, t=None, per_cell=False):
+    w = I.random_small(grid, seed, contrast_exp=contrast, bc=bc, per_cell=per_cell)
+    P = ffp.Preconditioner(grid, dev(w["kappa"]), bc, precision, t=None if t is None else dev(t))
+    bands = o.assemble(grid, w["kappa"], bc)
+    f = o.setup(grid, bands, t)
+    return w, P, bands, f
+
+
+# several tiles along x (S = 1..32 slots per lane), ragged tails, degenerate dims
+GRIDS = [(1, 1, 1), (1, 1, 5), (5, 1, 1), (1, 6, 1), (2, 2, 2), (3, 8, 2), (5, 6, 7), (33, 5, 4),
+         (17, 3, 9), (100, 4, 5), (64, 8, 6), (129, 3, 3), (350, 3, 4)]
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_assembly_parity(grid):
+    w, P, bands, _ = make(grid, 1)
+    ex = P.export()
+    for k, ref in zip(("d", "cx", "cy", "cz"), bands):
+        g = host(ex[k])
+        assert np.all(np.abs(g - ref) <= 1e-14 * np.abs(ref) + 1e-300), k
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_spmv_parity(grid):
+    w, P, bands, _ = make(grid, 2)
+    x = np.random.default_rng(3).standard_normal(int(np.prod(grid)))
+    y = host(P.spmv(dev(x)))
+    yr = o.spmv(grid, bands, x)
+    scale = o.spmv(grid, tuple(np.abs(b) for b in bands), np.abs(x))  # sum of |terms|
+    assert np.all(np.abs(y - yr) <= 1e-14 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_setup_factor_parity_fp64(grid):
+    """Stored bands l2 (y-band of P_i), l1 (x-band of T_k), 1/M vs the oracle."""
+    _, P, _, f = make(grid, 4)
+    ex = P.export()
+    for k, ref in (("l2", f.Py), ("l1", f.To), ("minv", 1.0 / f.M)):
+        g = host(ex[k])
+        err = np.abs(g - ref)
+        assert np.all(err <= 1e-10 * np.abs(ref) + 1e-300), (k, float(np.max(err / (np.abs(ref) + 1e-300))))
+
+
+def factors_of(P):
+    """The GPU's stored factors as an oracle Factors object (FP64)."""
+    ex = {k: host(v) for k, v in P.export().items()}
+    n = ex["d"].size
+    nan = np.full(n, np.nan)
+    return o.Factors(P.grid, ex["cz"], nan, nan, ex["l2"], nan, ex["l1"], 1.0 / ex["minv"]), ex
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_apply_kernel_parity_fp64(grid):
+    """The apply kernel against the oracle's Algorithms 1-7 on the same factors."""
+    _, P, _, f = make(grid, 5)
+    r = np.random.default_rng(6).standard_normal(int(np.prod(grid)))
+    z = host(P.apply(dev(r)))
+    fg, _ = factors_of(P)
+    assert relerr(z, o.apply(fg, r)) <= 1e-12
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_setup_and_apply_parity_fp64(grid):
+    _, P, _, f = make(grid, 5)
+    r = np.random.default_rng(6).standard_normal(int(np.prod(grid)))
+    z = host(P.apply(dev(r)))
+    assert relerr(z, o.apply(f, r)) <= 1e-10
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_apply_parity_fp32(grid):
+    _, P, _, f = make(grid, 7, precision="fp32")
+    r = np.random.default_rng(8).standard_normal(int(np.prod(grid)))
+    z = host(P.apply(dev(r)))
+    zr = o.apply(f, r)
+    assert relerr(z, zr) <= 1e-5
+
+
+@pytest.mark.parametrize("grid", [(33, 5, 4), (64, 8, 6), (350, 3, 4)])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_apply_kernel_parity_reduced(grid, precision):
+    """FP32 arithmetic on FP32 / BF16 factors against the FP64 oracle applying
+    the same (exported) factors: only the FP32 rounding of the sweeps differs."""
+    _, P, _, _ = make(grid, 9, precision=precision)
+    r = np.random.default_rng(10).standard_normal(int(np.prod(grid)))
+    z = host(P.apply(dev(r)))
+    assert np.all(np.isfinite(z)) and relerr(z, o.apply(factors_of(P)[0], r)) <= 1e-5
+
+
+@pytest.mark.parametrize("grid", [(5, 6, 7), (33, 5, 4), (64, 8, 6), (17, 3, 9), (1, 1, 5), (350, 3, 4)])
+def test_combination_parity_fp64(grid):
+    """B_c (Sec. III Eq. (com)): ILU(0) pivots and the combined apply."""
+    w = I.random_small(grid, 31, contrast_exp=3)
+    P = ffp.Preconditioner(grid, dev(w["kappa"]), w["bc"], "fp64", precond="combo")
+    bands = o.assemble(grid, w["kappa"], w["bc"])
+    f = o.setup(grid, bands)
+    Dp = o.ilu0_setup(grid, bands)
+    fg, ex = factors_of(P)
+    np.testing.assert_allclose(ex["dinv"], 1.0 / Dp, rtol=1e-10)
+    r = np.random.default_rng(32).standard_normal(int(np.prod(grid)))
+    z = host(P.apply(dev(r)))
+    assert relerr(z, o.combo_apply(grid, bands, fg, 1.0 / ex["dinv"], r)) <= 1e-12
+    assert relerr(z, o.combo_apply(grid, bands, f, Dp, r)) <= 1e-10
+
+
+@pytest.mark.parametrize("grid", [(33, 5, 4), (64, 8, 6)])
+def test_combination_parity_fp32(grid):
+    w = I.random_small(grid, 33, contrast_exp=3)
+    P = ffp.Preconditioner(grid, dev(w["kappa"]), w["bc"], "fp32", precond="combo")
+    bands = o.assemble(grid, w["kappa"], w["bc"])
+    r = np.random.default_rng(34).standard_normal(int(np.prod(grid)))
+    zr = o.combo_apply(grid, bands, o.setup(grid, bands), o.ilu0_setup(grid, bands), r)
+    assert relerr(host(P.apply(dev(r))), zr) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_combination_pcg_blocks32(precision):
+    w = I.workload_blocks32(seed=0)
+    g, bc = w["grid"], w["bc"]
+    P = ffp.Preconditioner(g, dev(w["kappa"]), bc, precision, precond="combo")
+    x, st = P.solve(dev(w["b"]), rtol=1e-8, maxit=200)
+    bands = o.assemble(g, w["kappa"], bc)
+    ref = o.pcg(g, bands, o.setup(g, bands), w["b"], rtol=1e-8, maxit=200, flexible=True,
+                ilu=o.ilu0_setup(g, bands))
+    assert st["status"] == 0 and ref["status"] == 0 and st["rel_res_true"] < 1e-8
+    xr = host(x)
+    assert np.linalg.norm(w["b"] - o.spmv(g, bands, xr)) / np.linalg.norm(w["b"]) < 1e-8
+    if precision == "fp64":
+        assert abs(st["iters"] - ref["iters"]) <= 1
+        assert relerr(xr, ref["x"]) <= 1e-7
+    else:
+        assert st["iters"] <= ref["iters"] + 3
+
+
+def test_user_filter_parity():
+    grid = (9, 7, 6)
+    t = np.random.default_rng(11).uniform(0.5, 2.0, int(np.prod(grid)))
+    _, P, _, f = make(grid, 12, t=t)
+    ex = P.export()
+    assert np.max(np.abs(host(ex["minv"]) - 1.0 / f.M) / (1.0 / f.M)) <= 1e-10
+    r = np.random.default_rng(13).standard_normal(int(np.prod(grid)))
+    assert relerr(host(P.apply(dev(r))), o.apply(f, r)) <= 1e-10
+    assert relerr(host(P.apply(dev(r))), o.apply(factors_of(P)[0], r)) <= 1e-12
+
+
+@pytest.mark.parametrize("grid", [(1024, 2, 3), (1023, 3, 2)])
+def test_longest_line(grid):
+    _, P, _, f = make(grid, 14, contrast=2)
+    r = np.random.default_rng(15).standard_normal(int(np.prod(grid)))
+    assert relerr(host(P.apply(dev(r))), o.apply(factors_of(P)[0], r)) <= 1e-12
+    assert relerr(host(P.apply(dev(r))), o.apply(f, r)) <= 1e-10
+
+
+def test_pcg_parity_fp64_grf32():
+    """Plain B_NTD PCG (the rowsum NTD alone does not converge on the 10^6
+    block workload within maxit, on the oracle as on the GPU; the 10^2 GRF
+    converges)."""
+    w = I.workload_grf(seed=0, n=32, exponent=1.0)
+    g, bc = w["grid"], w["bc"]
+    P = ffp.Preconditioner(g, dev(w["kappa"]), bc, "fp64")
+    x, st = P.solve(dev(w["b"]), rtol=1e-8, maxit=1000)
+    bands = o.assemble(g, w["kappa"], bc)
+    ref = o.pcg(g, bands, o.setup(g, bands), w["b"], rtol=1e-8, maxit=1000)
+    assert st["status"] == 0 and ref["status"] == 0
+    assert abs(st["iters"] - ref["iters"]) <= 1
+    assert st["rel_res_true"] < 1e-8 and ref["relres"] < 1e-8
+    assert relerr(host(x), ref["x"]) <= 1e-7
+    # independent true residual with the oracle's operator
+    xr = host(x)
+    assert np.linalg.norm(w["b"] - o.spmv(g, bands, xr)) / np.linalg.norm(w["b"]) < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_flexible_cg_converges_grf32(precision):
+    w = I.workload_grf(seed=1, n=32, exponent=1.0)
+    g, bc = w["grid"], w["bc"]
+    P = ffp.Preconditioner(g, dev(w["kappa"]), bc, precision)
+    x, st = P.solve(dev(w["b"]), rtol=1e-8, maxit=1000)
+    bands = o.assemble(g, w["kappa"], bc)
+    ref = o.pcg(g, bands, o.setup(g, bands), w["b"], rtol=1e-8, maxit=1000)
+    assert st["status"] == 0 and st["rel_res_true"] < 1e-8
+    xr = host(x)
+    assert np.linalg.norm(w["b"] - o.spmv(g, bands, xr)) / np.linalg.norm(w["b"]) < 1e-8
+    if precision == "fp32":
+        assert st["iters"] <= ref["iters"] + 5
+
+
+def test_zero_rhs_and_warm_start():
+    grid = (6, 5, 4)
+    w, P, bands, f = make(grid, 16)
+    x, st = P.solve(dev(np.zeros(120)))
+    assert st["iters"] == 0 and st["status"] == 0 and not torch.any(x != 0)
+    x, st = P.solve(dev(w["b"]), rtol=1e-10)
+    x2, st2 = P.solve(dev(w["b"]), x=x.clone(), rtol=1e-10)
+    assert st2["iters"] == 0 and st2["rel_res_true"] < 1e-10
+
+
+def test_bad_arguments_rejected():
+    grid = (4, 4, 4)
+    k = np.ones(64)
+    k[5] = -1.0
+    with pytest.raises(ffp.FFPError) as e:
+        ffp.Preconditioner(grid, dev(k), I.BC_Z_DIRICHLET)
+    assert e.value.status == ffp.FFP_ERR_ARG
+    k[5] = np.nan
+    with pytest.raises(ffp.FFPError):
+        ffp.Preconditioner(grid, dev(k), I.BC_Z_DIRICHLET)
+    t = np.ones(64)
+    t[3] = 0.0
+    with pytest.raises(ffp.FFPError) as e:
+        ffp.Preconditioner(grid, dev(np.ones(64)), I.BC_Z_DIRICHLET, t=dev(t))
+    assert e.value.status == ffp.FFP_ERR_ARG
+    with pytest.raises(ffp.FFPError):
+        ffp.Preconditioner((ffp.FFP_MAX_NX + 1, 1, 1), dev(np.ones(ffp.FFP_MAX_NX + 1)),
+                           I.BC_Z_DIRICHLET)
+
+
+def test_pure_neumann_breakdown_reported():
+    """All-Neumann: A is singular (constant null vector), so the rowsum-filtered
+    factorization reaches a zero pivot on the last eliminated block; the setup
+    reports a breakdown (or, if rounding keeps the pivot positive, the
+    preconditioner is still applied without fault)."""
+    grid = (4, 3, 3)
+    try:
+        ffp.Preconditioner(grid, dev(np.ones(36)), (1, 1, 1, 1, 1, 1))
+    except ffp.FFPError as e:
+        assert e.status == ffp.FFP_ERR_BREAKDOWN
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_apply_symmetric_positive_layered128(precision):
+    """At the 128^3 layered workload size: B^{-1} is symmetric and positive
+    definite (properties that hold at any size): <B^-1 u, v> = <u, B^-1 v>,
+    <u, B^-1 u> > 0; and repeated applies are bitwise identical."""
+    w = I.workload_layered128(seed=0)
+    P = ffp.Preconditioner(w["grid"], dev(w["kappa"]), w["bc"], precision)
+    rng = np.random.default_rng(17)
+    u = dev(rng.standard_normal(w["kappa"].size))
+    v = dev(rng.standard_normal(w["kappa"].size))
+    Bu, Bv = P.apply(u), P.apply(v)
+    a, b = float(torch.dot(Bu, v)), float(torch.dot(u, Bv))
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert abs(a - b) <= tol * (float(torch.norm(Bu)) * float(torch.norm(v)))
+    assert float(torch.dot(u, Bu)) > 0
+    assert torch.equal(P.apply(u), Bu)
