@@ -78,6 +78,10 @@ typedef struct {
     double rel_res;       /* recursive ||r|| / ||b|| at exit */
     double rel_res_true;  /* ||b - A x|| / ||b|| recomputed at exit */
     double solve_s;       /* wall time of the solve (host clock, after a stream sync) */
+    double precond_ms;    /* device time of all preconditioner applies (CUDA events on `stream`) */
+    double ntd_ms;        /* device time of their B_NTD sweeps (the apply kernels) */
+    int napply;           /* number of preconditioner applies */
+    long long launches;   /* kernels this call launched */
 } ffp_stats;
 
 typedef struct ffp_handle ffp_handle;

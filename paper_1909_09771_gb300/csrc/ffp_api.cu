@@ -17,6 +17,7 @@ struct ffp_handle {
     KernelCtx c;
     int device;
     double *host_scal;  // pinned copy of the scalar block + flags
+    cudaEvent_t ev[3];  // preconditioner timing: start, NTD start, end
 };
 
 namespace {
@@ -78,14 +79,33 @@ constexpr size_t kScalBytes = 8 * (size_t)kScal + 4 * 16;
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? FFP_OK : FFP_ERR_CUDA; }
 
-// z = B^{-1} r for the handle's preconditioner (r and z distinct from c1, c2)
-cudaError_t precond_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st) {
-    if (c.precond != FFP_PRECOND_COMBO) return launch_apply(c, r, z, st);
-    // B_c^{-1} r = y + B_NTD^{-1} (r - A y), y = B_ILU0^{-1} r
-    cudaError_t e = launch_ilu_solve(c, r, c.ws.c1, st);
-    if (e == cudaSuccess) e = launch_resid_vec(c, r, c.ws.c1, c.ws.c2, st);
-    if (e == cudaSuccess) e = launch_apply(c, c.ws.c2, z, st);
-    if (e == cudaSuccess) e = launch_add(c, z, c.ws.c1, st);
+// kernels launched by one B_NTD apply / one ILU(0) solve
+long long ntd_launches(const KernelCtx &c) {
+    const int mz = (c.nz - 1) / 2;
+    return (mz > 0 || c.nz - 1 - mz > 0) ? 3 : 1;
+}
+long long ilu_launches(const KernelCtx &c) { return 2LL * (c.ny + c.nz - 1); }
+
+// z = B^{-1} r for the handle's preconditioner (r and z distinct from c1, c2).
+// ev (optional): events recorded at the start, before the NTD sweeps and at the end.
+cudaError_t precond_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
+                          long long *launches, cudaEvent_t *ev = nullptr) {
+    cudaError_t e = cudaSuccess;
+    if (ev) e = cudaEventRecord(ev[0], st);
+    if (c.precond != FFP_PRECOND_COMBO) {
+        if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = launch_apply(c, r, z, st);
+        *launches += ntd_launches(c);
+    } else {
+        // B_c^{-1} r = y + B_NTD^{-1} (r - A y), y = B_ILU0^{-1} r
+        if (e == cudaSuccess) e = launch_ilu_solve(c, r, c.ws.c1, st);
+        if (e == cudaSuccess) e = launch_resid_vec(c, r, c.ws.c1, c.ws.c2, st);
+        if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = launch_apply(c, c.ws.c2, z, st);
+        if (e == cudaSuccess) e = launch_add(c, z, c.ws.c1, st);
+        *launches += ilu_launches(c) + 2 + ntd_launches(c);
+    }
+    if (ev && e == cudaSuccess) e = cudaEventRecord(ev[2], st);
     return e;
 }
 
@@ -130,6 +150,8 @@ int ffp_setup(const ffp_grid *grid, const double *kappa, const ffp_bc *bc, int f
     std::memset(h, 0, sizeof(*h));
     if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return FFP_ERR_CUDA; }
     if (cudaMallocHost((void **)&h->host_scal, kScalBytes) != cudaSuccess) { delete h; return FFP_ERR_CUDA; }
+    for (int k = 0; k < 3; ++k)
+        if (cudaEventCreate(&h->ev[k]) != cudaSuccess) { ffp_destroy(h); return FFP_ERR_CUDA; }
     KernelCtx &c = h->c;
     c.nx = grid->nx; c.ny = grid->ny; c.nz = grid->nz;
     c.n = (long long)c.nx * c.ny * c.nz;
@@ -171,7 +193,8 @@ int ffp_spmv(ffp_handle *h, const double *x, double *y, void *stream) {
 
 int ffp_apply(ffp_handle *h, const double *r, double *z, void *stream) {
     if (!h || !r || !z || r == z) return FFP_ERR_ARG;
-    return cuda_status(precond_apply(h->c, r, z, (cudaStream_t)stream));
+    long long n = 0;
+    return cuda_status(precond_apply(h->c, r, z, (cudaStream_t)stream, &n));
 }
 
 int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, double *l2,
@@ -201,6 +224,8 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
     auto t0 = std::chrono::steady_clock::now();
     int it = 0, fresh = 1, status = FFP_OK;
     double bb = 0.0, rr = 0.0;
+    double pre_ms = 0.0, ntd_ms = 0.0;
+    long long nl = 0;
 #define FFP_TRY(expr)                                                 \
     do {                                                              \
         cudaError_t _e = (expr);                                      \
@@ -209,14 +234,15 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
     FFP_TRY(cudaMemsetAsync(c.ws.flags, 0, 4 * 16, st));
     FFP_TRY(launch_resid(c, b, x, st));
     FFP_TRY(launch_finalize(c, FIN_RESID, 0, flexible, st));
+    nl += 2;
     if ((status = read_scalars(h, st)) != FFP_OK) goto done;
     bb = h->host_scal[SC_BB];
     rr = h->host_scal[SC_RR];
     if (bb == 0.0) {
         FFP_TRY(cudaMemsetAsync(x, 0, 8 * (size_t)c.n, st));
         if (stats) {
-            stats->iters = 0; stats->status = FFP_OK; stats->rel_res = 0.0;
-            stats->rel_res_true = 0.0; stats->solve_s = 0.0;
+            std::memset(stats, 0, sizeof(*stats));
+            stats->launches = nl;
         }
         cudaStreamSynchronize(st);
         return FFP_OK;
@@ -226,13 +252,14 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
             // confirm with the true residual; continue from it if it is not converged
             FFP_TRY(launch_resid(c, b, x, st));
             FFP_TRY(launch_finalize(c, FIN_RESID, 0, flexible, st));
+            nl += 2;
             if ((status = read_scalars(h, st)) != FFP_OK) goto done;
             rr = h->host_scal[SC_RR];
             if (std::sqrt(rr / bb) < rtol) break;
             fresh = 1;
         }
         if (it >= maxit) { status = FFP_ERR_NOT_CONVERGED; break; }
-        FFP_TRY(precond_apply(c, c.ws.r, c.ws.z, st));
+        FFP_TRY(precond_apply(c, c.ws.r, c.ws.z, st, &nl, h->ev));
         FFP_TRY(launch_dot_rz(c, st));
         FFP_TRY(launch_finalize(c, FIN_RZ, fresh, flexible, st));
         FFP_TRY(launch_update_p(c, fresh, st));
@@ -241,8 +268,14 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
         FFP_TRY(launch_finalize(c, FIN_PQ, 0, flexible, st));
         FFP_TRY(launch_update_xr(c, x, st));
         FFP_TRY(launch_finalize(c, FIN_RR, 0, flexible, st));
+        nl += 8;
         ++it;
         if ((status = read_scalars(h, st)) != FFP_OK) goto done;
+        {
+            float a = 0.f, b2 = 0.f;
+            if (cudaEventElapsedTime(&a, h->ev[0], h->ev[2]) == cudaSuccess) pre_ms += a;
+            if (cudaEventElapsedTime(&b2, h->ev[1], h->ev[2]) == cudaSuccess) ntd_ms += b2;
+        }
         if (host_flags(h)[FL_PQ]) { status = FFP_ERR_BREAKDOWN; break; }
         rr = h->host_scal[SC_RR];
         if (!std::isfinite(rr)) { status = FFP_ERR_BREAKDOWN; break; }
@@ -252,6 +285,9 @@ done:
     if (stats) {
         stats->iters = it;
         stats->status = status;
+        stats->precond_ms = pre_ms;
+        stats->ntd_ms = ntd_ms;
+        stats->napply = it;
         stats->rel_res = (bb > 0.0) ? std::sqrt(rr / bb) : 0.0;
         stats->rel_res_true = -1.0;
         if (status != FFP_ERR_CUDA) {
@@ -259,7 +295,9 @@ done:
                 launch_finalize(c, FIN_RESID, 0, flexible, st) == cudaSuccess &&
                 read_scalars(h, st) == FFP_OK)
                 stats->rel_res_true = std::sqrt(h->host_scal[SC_TRR] / bb);
+            nl += 2;
         }
+        stats->launches = nl;
         stats->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return status;
@@ -267,6 +305,8 @@ done:
 
 void ffp_destroy(ffp_handle *h) {
     if (!h) return;
+    for (int k = 0; k < 3; ++k)
+        if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     if (h->host_scal) cudaFreeHost(h->host_scal);
     delete h;
 }

@@ -44,7 +44,9 @@ class BC(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
-                ("rel_res_true", ctypes.c_double), ("solve_s", ctypes.c_double)]
+                ("rel_res_true", ctypes.c_double), ("solve_s", ctypes.c_double),
+                ("precond_ms", ctypes.c_double), ("ntd_ms", ctypes.c_double),
+                ("napply", ctypes.c_int), ("launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -127,6 +129,14 @@ def _dev_vec(x, n, name):
     return x
 
 
+def setup_launches(grid, precond="ntd", user_t=False):
+    """Kernels one ffp_setup launches (assembly, filter check, band conversion,
+    setup phases, ILU(0) pivot diagonals)."""
+    nx, ny, nz = grid
+    n = 1 + (1 if user_t else 0) + (3 if precond == "combo" else 1) + (2 if nz > 1 else 1)
+    return n + ((ny + nz - 1) if precond == "combo" else 0)
+
+
 class Preconditioner:
     """Operator A (assembled from kappa) and its preconditioner B on the
     current CUDA device: precond "ntd" (B_NTD, Sec. II) or "combo" (B_c with the
@@ -134,7 +144,7 @@ class Preconditioner:
     this object; the library only points into it."""
 
     def __init__(self, grid, kappa, bc, precision="fp64", t=None, lengths=(1.0, 1.0, 1.0),
-                 stream=None, precond="ntd"):
+                 stream=None, precond="ntd", workspace=None):
         lib = load()
         self.grid = tuple(int(v) for v in grid)
         self.n = self.grid[0] * self.grid[1] * self.grid[2]
@@ -145,7 +155,12 @@ class Preconditioner:
         if nbytes == 0:
             raise FFPError(FFP_ERR_ARG, "ffp_workspace_bytes")
         dev = kappa.device
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        elif not (workspace.is_cuda and workspace.dtype == torch.uint8 and workspace.numel() >= nbytes
+                  and workspace.data_ptr() % 256 == 0):
+            raise ValueError(f"workspace must be a 256-byte aligned CUDA uint8 tensor of >= {nbytes} bytes")
+        self.workspace = workspace
         kappa = _dev_vec(kappa, self.n, "kappa")
         if t is not None:
             t = _dev_vec(t, self.n, "t")
