@@ -159,6 +159,35 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
 int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, double *l2,
                double *l1, double *minv, double *dinv, void *stream);
 
+/* Allocation-free apply.  The paper has no counterpart: this exists for callers
+ * that cannot allocate device memory at the point where they apply the
+ * preconditioner -- for example code running under a host framework that owns
+ * every device allocation (a fixed memory pool, an inference runtime, a plugin
+ * inside another program's CUDA context), or code that must not call
+ * cudaMalloc at all in its steady state.  Such a caller can still build the
+ * handle once (its workspace is caller memory, allocated however the caller
+ * may) and then call this entry point, which calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * It computes z = B_NTD^{-1} r with the same kernels as ffp_apply, using the
+ * handle's factors; for a handle built with FFP_PRECOND_COMBO it applies only
+ * the nested sweeps B_NTD^{-1}, not the combination B_c.  The two planes of
+ * scratch the upper sweeps need live in a fixed array in the library's device
+ * image (2 * FFP_NOALLOC_MAX_PLANE FP64 values, 2 MiB), which every GPU that
+ * loads the library holds until the process exits.
+ *   h       handle from ffp_setup; its device must be the current device
+ *   r, z    device FP64 [N], distinct (as for ffp_apply)
+ * Returns FFP_ERR_ARG if nx * ny > FFP_NOALLOC_MAX_PLANE (the grid's planes do
+ * not fit the fixed scratch) or if the current device is not the handle's.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture on that device.  All calls share the
+ * one array: calls whose kernels overlap on the GPU (on different streams, or
+ * from several host threads) race on it and must be serialised by the caller.
+ * Nothing in the array needs clearing: each call writes every scratch entry
+ * before reading it. */
+#define FFP_NOALLOC_MAX_PLANE 131072
+int ffp_apply_noalloc(ffp_handle *h, const double *r, double *z, void *stream);
+
 /* Free the host handle (no device memory is freed). */
 void ffp_destroy(ffp_handle *h);
 

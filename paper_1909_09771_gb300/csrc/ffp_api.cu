@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "ffp_kernels.h"
@@ -324,3 +325,42 @@ const char *ffp_strerror(int status) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free apply
+// Scratch for ffp_apply_noalloc: the two upper-sweep planes of the B_NTD apply.
+// In host code `g_noalloc_scratch` is only a host-side stand-in for the symbol;
+// its device address is looked up once per device and cached.
+static __device__ __align__(256) double g_noalloc_scratch[2 * FFP_NOALLOC_MAX_PLANE];
+
+namespace {
+constexpr int kMaxDevices = 256;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set up on first use).
+int noalloc_scratch(int device, double **out) {
+    if (device < 0 || device >= kMaxDevices) return FFP_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FFP_ERR_CUDA;
+        g_noalloc_ptr[device] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return FFP_OK;
+}
+}  // namespace
+
+extern "C" int ffp_apply_noalloc(ffp_handle *h, const double *r, double *z, void *stream) {
+    if (!h || !r || !z || r == z) return FFP_ERR_ARG;
+    if ((long long)h->c.nx * h->c.ny > FFP_NOALLOC_MAX_PLANE) return FFP_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFP_ERR_CUDA;
+    if (dev != h->device) return FFP_ERR_ARG;
+    double *scr = nullptr;
+    const int st = noalloc_scratch(dev, &scr);
+    if (st != FFP_OK) return st;
+    KernelCtx c = h->c;
+    c.ws.ascr = scr;
+    return cuda_status(launch_apply(c, r, z, (cudaStream_t)stream));
+}
