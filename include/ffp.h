@@ -152,12 +152,12 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
 
 /* Copy the stored operator and factors out as FP64 device arrays [N] each (any
  * pointer may be NULL): d, cx, cy, cz = bands of A (cx[a] = A[a, a+1], cy[a] =
- * A[a, a+nx], cz[a] = A[a, a+nx*ny], zero where there is no neighbour);
- * l2 = y-band of every P_i, l1 = x-band of every T_k, minv = 1 / M (level-1
- * pivots) -- the band storage of Sec. II-A, in the stored precision; dinv =
- * 1 / D, the ILU(0) pivots (B_c only, else left untouched). */
-int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, double *l2,
-               double *l1, double *minv, double *dinv, void *stream);
+ * A[a, a+nx], cz[a] = A[a, a+nx*ny], zero where there is no neighbour); the
+ * band storage of Sec. II-A in the stored precision: l3 = z-band of A, l2 =
+ * y-band of every P_i, l1 = x-band of every T_k, minv = 1 / M (level-1
+ * pivots); dinv = 1 / D, the ILU(0) pivots (B_c only, else left untouched). */
+int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, double *l3,
+               double *l2, double *l1, double *minv, double *dinv, void *stream);
 
 /* Allocation-free apply.  The paper has no counterpart: this exists for callers
  * that cannot allocate device memory at the point where they apply the

@@ -55,7 +55,10 @@ size_t carve(const ffp_grid *g, int prec, char *base, Ws *ws) {
     std::memset(&w, 0, sizeof(w));
     w.d = (double *)take(8 * n); w.cx = (double *)take(8 * n);
     w.cy = (double *)take(8 * n); w.cz = (double *)take(8 * n);
-    w.l1 = take(fb * n); w.minv = take(fb * n); w.l2 = take(fb * n); w.l3 = take(fb * n);
+    const int S = slots_for(g->nx);
+    const size_t nlines = (size_t)g->ny * g->nz;
+    w.rec = take(fb * nlines * (size_t)rec_len(S > 0 ? S : 1));
+    w.l3 = take(fb * n);
     w.dinv = take(fb * n); w.lx = take(fb * n); w.ly = take(fb * n);
     w.r = (double *)take(8 * n); w.z = (double *)take(8 * n);
     w.p = (double *)take(8 * n); w.q = (double *)take(8 * n);
@@ -165,6 +168,9 @@ int ffp_setup(const ffp_grid *grid, const double *kappa, const ffp_bc *bc, int f
     carve(grid, precision, (char *)workspace, &c.ws);
 
     cudaError_t e = cudaMemsetAsync(c.ws.scal, 0, kScalBytes, st);
+    if (e == cudaSuccess)   // record pads must read as 0
+        e = cudaMemsetAsync(c.ws.rec, 0,
+                            prec_bytes(precision) * (size_t)c.ny * c.nz * (size_t)rec_len(slots), st);
     if (e == cudaSuccess) e = launch_assemble(c, kappa, bc->face, st);
     if (e == cudaSuccess && filter == FFP_FILTER_USER) e = launch_check_filter(c, t, st);
     int status = cuda_status(e);
@@ -198,8 +204,8 @@ int ffp_apply(ffp_handle *h, const double *r, double *z, void *stream) {
     return cuda_status(precond_apply(h->c, r, z, (cudaStream_t)stream, &n));
 }
 
-int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, double *l2,
-               double *l1, double *minv, double *dinv, void *stream) {
+int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, double *l3,
+               double *l2, double *l1, double *minv, double *dinv, void *stream) {
     if (!h) return FFP_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nb = 8 * (size_t)h->c.n;
@@ -208,9 +214,10 @@ int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, dou
     if (cx && e == cudaSuccess) e = cudaMemcpyAsync(cx, h->c.ws.cx, nb, cudaMemcpyDeviceToDevice, st);
     if (cy && e == cudaSuccess) e = cudaMemcpyAsync(cy, h->c.ws.cy, nb, cudaMemcpyDeviceToDevice, st);
     if (cz && e == cudaSuccess) e = cudaMemcpyAsync(cz, h->c.ws.cz, nb, cudaMemcpyDeviceToDevice, st);
-    if (l2 && e == cudaSuccess) e = launch_export(h->c, h->c.ws.l2, l2, st);
-    if (l1 && e == cudaSuccess) e = launch_export(h->c, h->c.ws.l1, l1, st);
-    if (minv && e == cudaSuccess) e = launch_export(h->c, h->c.ws.minv, minv, st);
+    if (l3 && e == cudaSuccess) e = launch_export_rec(h->c, 3, l3, st);
+    if (l2 && e == cudaSuccess) e = launch_export_rec(h->c, 2, l2, st);
+    if (l1 && e == cudaSuccess) e = launch_export_rec(h->c, 0, l1, st);
+    if (minv && e == cudaSuccess) e = launch_export_rec(h->c, 1, minv, st);
     if (dinv && e == cudaSuccess && h->c.precond == FFP_PRECOND_COMBO)
         e = launch_export(h->c, h->c.ws.dinv, dinv, st);
     return cuda_status(e);

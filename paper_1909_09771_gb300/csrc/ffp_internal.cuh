@@ -260,6 +260,56 @@ __device__ __forceinline__ void twisted_pivots(int cnt, int lane, const double (
     bad = b_;
 }
 
+// ---------------------------------------------------------------- factor line records
+// The apply reads the stored factors line by line in the warp's own order, so
+// they are stored as one record per line (i, k), record index i*ny + k:
+//   field 0 eout[S][32]  coupling of the cell towards the twist cell
+//                        (top chain: l1[a]; bottom chain: l1[a-1])
+//   field 1 minv[S][32]  1 / M_a
+//   field 2 l2[S][32]    y-band of P_i: coupling of cell a of line k with line k+1
+//   field 3 l3[S][32]    z-band of A: coupling of cell a of plane i with plane i+1
+//   mid[8]               the twist cell: 1/M_m, T[m-1,m], T[m,m+1], l2, l3, 0, 0, 0
+// [s][32] is slot s of lanes 0..31; pads hold 0.  A record is a multiple of 16
+// bytes, so a warp pulls it with 16-byte asynchronous copies.
+enum { REC_EOUT = 0, REC_MINV = 1, REC_L2 = 2, REC_L3 = 3, REC_NFIELD = 4 };
+enum { MID_MINV = 0, MID_EM1 = 1, MID_EM = 2, MID_L2 = 3, MID_L3 = 4, REC_NMID = 8 };
+
+__host__ __device__ __forceinline__ long rec_len(int S) { return (long)REC_NFIELD * 32 * S + REC_NMID; }
+
+// Offset inside a record of field f at cell a of an nx-cell line (the twist
+// cell maps to mid + midf).
+__host__ __device__ __forceinline__ long rec_cell(int nx, int S, int f, int midf, int a) {
+    const int m = (nx - 1) / 2;
+    if (a == m) return (long)REC_NFIELD * 32 * S + midf;
+    int c, lane;
+    if (a < m) { c = a; lane = c / S; }
+    else { c = nx - 1 - a; lane = 16 + c / S; }
+    return (long)f * 32 * S + (long)(c % S) * 32 + lane;
+}
+
+// ---------------------------------------------------------------- async copies
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_dyn(int n) {
+    switch (n) {
+        case 0: cp_async_wait<0>(); break;
+        case 1: cp_async_wait<1>(); break;
+        case 2: cp_async_wait<2>(); break;
+        case 3: cp_async_wait<3>(); break;
+        case 4: cp_async_wait<4>(); break;
+        default: cp_async_wait<5>(); break;
+    }
+}
+
 // ---------------------------------------------------------------- misc
 __device__ __forceinline__ void named_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -283,8 +333,9 @@ inline int slots_for(int nx) {
 struct Ws {
     // operator bands (FP64)
     double *d, *cx, *cy, *cz;
-    // factors in storage precision: l1 (x-band of T), minv (1/M), l2 (y-band of P), l3 (z-band of A)
-    void *l1, *minv, *l2, *l3;
+    // factors in storage precision: one record per line (see rec_len), and l3 =
+    // z-band of A in natural order (for the ILU(0) sweeps)
+    void *rec, *l3;
     // combination preconditioner: ILU(0) 1/D and the x, y bands of A in storage precision
     void *dinv, *lx, *ly;
     // combination temporaries

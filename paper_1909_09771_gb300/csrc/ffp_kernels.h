@@ -28,6 +28,8 @@ cudaError_t launch_resid_vec(const KernelCtx &c, const double *r, const double *
 cudaError_t launch_add(const KernelCtx &c, double *z, const double *y, cudaStream_t st);  // z += y
 cudaError_t launch_spmv(const KernelCtx &c, const double *x, double *y, cudaStream_t st);
 cudaError_t launch_export(const KernelCtx &c, const void *src, double *dst, cudaStream_t st);
+// natural-order band from the factor records: 0 = l1, 1 = 1/M, 2 = l2, 3 = l3
+cudaError_t launch_export_rec(const KernelCtx &c, int what, double *dst, cudaStream_t st);
 // CG building blocks (FP64); each fills ws.red with per-block partial sums and
 // finalize() folds them, in a fixed order, into the scalar block ws.scal.
 cudaError_t launch_resid(const KernelCtx &c, const double *b, const double *x, cudaStream_t st);

@@ -73,6 +73,40 @@ __global__ void export_kernel(long long n, const F *__restrict__ s, double *o) {
         o[a] = (double)to_r(s[a], typename Compute<F>::type());
 }
 
+// l3 (z-band) into the factor line records
+template <typename F>
+__global__ void l3_records_kernel(Geo g, int S, const double *__restrict__ cz, F *rec) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(a % g.nx);
+        const long long line = a / g.nx;
+        rec[line * rec_len(S) + rec_cell(g.nx, S, REC_L3, MID_L3, x)] = from_d<F>(cz[a]);
+    }
+}
+
+// natural-order l1 (x-band of T), 1/M, l2 or l3 from the records (what: 0..3)
+template <typename F>
+__global__ void export_rec_kernel(Geo g, int S, const F *__restrict__ rec, int what, double *o) {
+    using R = typename Compute<F>::type;
+    const int m = (g.nx - 1) / 2;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(a % g.nx);
+        const F *rb = rec + (a / g.nx) * rec_len(S);
+        double v = 0.0;
+        if (what == 1) v = (double)to_r(rb[rec_cell(g.nx, S, REC_MINV, MID_MINV, x)], R());
+        else if (what == 2) v = (double)to_r(rb[rec_cell(g.nx, S, REC_L2, MID_L2, x)], R());
+        else if (what == 3) v = (double)to_r(rb[rec_cell(g.nx, S, REC_L3, MID_L3, x)], R());
+        else {
+            // T[x, x+1]: eout of x in the top chain, of x+1 in the bottom chain
+            if (x < m) v = (double)to_r(rb[rec_cell(g.nx, S, REC_EOUT, 0, x)], R());
+            else if (x == m) v = (x + 1 < g.nx) ? (double)to_r(rb[(long)REC_NFIELD * 32 * S + MID_EM], R()) : 0.0;
+            else v = (x + 1 < g.nx) ? (double)to_r(rb[rec_cell(g.nx, S, REC_EOUT, 0, x + 1)], R()) : 0.0;
+        }
+        o[a] = v;
+    }
+}
+
 // (A x)_a with the oracle's term order.
 __device__ __forceinline__ double stencil(const Geo &g, long long a, const double *__restrict__ d,
                                           const double *__restrict__ cx,
@@ -303,9 +337,13 @@ cudaError_t launch_check_filter(const KernelCtx &c, const double *t, cudaStream_
     return cudaGetLastError();
 }
 
+static Geo geo(const KernelCtx &c);
+static int grid_for(long long n);
+
 template <typename F>
 static void convert_all(const KernelCtx &c, cudaStream_t st) {
     convert_kernel<F><<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.ws.cz, (F *)c.ws.l3);
+    l3_records_kernel<F><<<grid_for(c.n), kThreads, 0, st>>>(geo(c), c.slots, c.ws.cz, (F *)c.ws.rec);
     if (c.precond == FFP_PRECOND_COMBO) {
         convert_kernel<F><<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.ws.cx, (F *)c.ws.lx);
         convert_kernel<F><<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.ws.cy, (F *)c.ws.ly);
@@ -317,6 +355,20 @@ cudaError_t launch_convert_bands(const KernelCtx &c, cudaStream_t st) {
         case FFP_FP64: convert_all<double>(c, st); break;
         case FFP_FP32: convert_all<float>(c, st); break;
         default: convert_all<__nv_bfloat16>(c, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_rec(const KernelCtx &c, int what, double *dst, cudaStream_t st) {
+    switch (c.prec) {
+        case FFP_FP64:
+            export_rec_kernel<double><<<grid_for(c.n), kThreads, 0, st>>>(geo(c), c.slots, (const double *)c.ws.rec, what, dst);
+            break;
+        case FFP_FP32:
+            export_rec_kernel<float><<<grid_for(c.n), kThreads, 0, st>>>(geo(c), c.slots, (const float *)c.ws.rec, what, dst);
+            break;
+        default:
+            export_rec_kernel<__nv_bfloat16><<<grid_for(c.n), kThreads, 0, st>>>(geo(c), c.slots, (const __nv_bfloat16 *)c.ws.rec, what, dst);
     }
     return cudaGetLastError();
 }

@@ -27,10 +27,10 @@ namespace ffp {
 
 struct SetupArgs {
     int nx, ny, nz;
-    int prec;  // storage precision of l1, minv, l2
+    int prec;  // storage precision of the factor records
     const double *d, *cx, *cy, *cz;
     const double *t;  // filter, NULL = rowsum
-    void *l1, *minv, *l2;
+    void *rec;        // factor line records (rec_len(S) entries per line)
     Ws ws;
 };
 
@@ -163,25 +163,31 @@ __device__ __forceinline__ void factor_line(const LineMap &L, int lane, int cnt,
     __syncwarp();
 }
 
+// Store line k of the plane: FP64 natural-order copies for the setup's own
+// plane solves (l1d, mid) and the line record line0 + k (eout, 1/M, twist cell).
 template <int S>
 __device__ __forceinline__ void store_line(const LineMap &L, int lane, int cnt, int nx, int k,
                                            const LineState<S> &st, double *l1d, double *mid,
-                                           void *l1f, void *mif, long goff, int prec) {
+                                           void *rec, long line0, int prec) {
     const long o = (long)k * nx;
+    const long rb = (line0 + k) * rec_len(S);
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+    for (int s = 0; s < S; ++s) {
         if (s < cnt) {
             const int a = slot_cell<S>(L, lane, s);
             l1d[o + a] = st.To[s];
             mid[o + a] = st.f.minv[s];
-            put_factor(l1f, goff + o + a, st.To[s], prec);
-            put_factor(mif, goff + o + a, st.f.minv[s], prec);
         }
+        put_factor(rec, rb + (long)REC_EOUT * 32 * S + s * 32 + lane, s < cnt ? st.f.eout[s] : 0.0, prec);
+        put_factor(rec, rb + (long)REC_MINV * 32 * S + s * 32 + lane, s < cnt ? st.f.minv[s] : 0.0, prec);
+    }
     if (lane == 0) {
         l1d[o + L.m] = st.Tom;
         mid[o + L.m] = st.f.minv_m;
-        put_factor(l1f, goff + o + L.m, st.Tom, prec);
-        put_factor(mif, goff + o + L.m, st.f.minv_m, prec);
+        const long mb = rb + (long)REC_NFIELD * 32 * S;
+        put_factor(rec, mb + MID_MINV, st.f.minv_m, prec);
+        put_factor(rec, mb + MID_EM1, st.f.em1, prec);
+        put_factor(rec, mb + MID_EM, st.f.em, prec);
     }
 }
 
@@ -191,7 +197,7 @@ __device__ __forceinline__ void store_line(const LineMap &L, int lane, int cnt, 
 template <int S>
 __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
                              const double *Px, const double *Py, const double *tp, double *l1d,
-                             double *mid, void *l1f, void *mif, long goff, int prec, double *lbuf,
+                             double *mid, void *rec, long line0, int prec, double *lbuf,
                              double *meet, int wid, int lane, int cnt, int *flags) {
     const int my = (ny - 1) / 2;
     const int nl = (wid == 0) ? my : ny - 1 - my;
@@ -223,7 +229,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
             Tom -= com;
         }
         factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags);
-        store_line<S>(L, lane, cnt, nx, k, st, l1d, mid, l1f, mif, goff, prec);
+        store_line<S>(L, lane, cnt, nx, k, st, l1d, mid, rec, line0, prec);
     }
     // twist line: Schur terms from both halves
     {
@@ -260,7 +266,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
         Tdm = Pd[o + L.m] - meet[L.m] - meet[2 * nx + L.m];
         Tom = Px[o + L.m] - meet[nx + L.m] - meet[3 * nx + L.m];
         factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags);
-        if (wid == 0) store_line<S>(L, lane, cnt, nx, my, st, l1d, mid, l1f, mif, goff, prec);
+        if (wid == 0) store_line<S>(L, lane, cnt, nx, my, st, l1d, mid, rec, line0, prec);
     }
 }
 
@@ -290,10 +296,13 @@ __global__ void __launch_bounds__(256) setup_kernel(SetupArgs A, int phase) {
             } else {
                 Pd = A.ws.sP[h][t & 1][0]; Px = A.ws.sP[h][t & 1][1]; Py = A.ws.sP[h][t & 1][2];
             }
-            for (long e = tid; e < nxy; e += blockDim.x) put_factor(A.l2, i * nxy + e, Py[e], A.prec);
+            for (long e = tid; e < nxy; e += blockDim.x)
+                put_factor(A.rec, ((long)i * ny + e / nx) * rec_len(S) +
+                                      rec_cell(nx, S, REC_L2, MID_L2, (int)(e % nx)),
+                           Py[e], A.prec);
             if (wid < 2)
                 level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + i * nxy : nullptr, l1d, mid,
-                                A.l1, A.minv, i * nxy, A.prec, lbuf, meet, wid, lane, cnt, flags);
+                                A.rec, (long)i * ny, A.prec, lbuf, meet, wid, lane, cnt, flags);
             const int dst = (t == nl3 - 1) ? mz : ((h == 0) ? i + 1 : i - 1);
             const int ic = (i < dst) ? i : dst;
             const double *C = A.cz + ic * nxy;
@@ -346,13 +355,15 @@ __global__ void __launch_bounds__(256) setup_kernel(SetupArgs A, int phase) {
             if (mz > 0) { vd -= A.ws.sC[0][0][e]; vx -= A.ws.sC[0][1][e]; vy -= A.ws.sC[0][2][e]; }
             if (mz < nz - 1) { vd -= A.ws.sC[1][0][e]; vx -= A.ws.sC[1][1][e]; vy -= A.ws.sC[1][2][e]; }
             Pd[e] = vd; Px[e] = vx; Py[e] = vy;
-            put_factor(A.l2, g0 + e, vy, A.prec);
+            put_factor(A.rec, ((long)mz * ny + e / nx) * rec_len(S) +
+                                  rec_cell(nx, S, REC_L2, MID_L2, (int)(e % nx)),
+                       vy, A.prec);
         }
         __syncthreads();
         if (wid < 2)
             level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + g0 : nullptr, A.ws.sF[0][0],
-                            A.ws.sF[0][1], A.l1, A.minv, g0, A.prec, lbuf, meet, wid, lane, cnt,
-                            flags);
+                            A.ws.sF[0][1], A.rec, (long)mz * ny, A.prec, lbuf, meet, wid, lane,
+                            cnt, flags);
     }
 }
 
@@ -362,7 +373,7 @@ cudaError_t setup_for_slots(const KernelCtx &c, const double *t, cudaStream_t st
     a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.prec = c.prec;
     a.d = c.ws.d; a.cx = c.ws.cx; a.cy = c.ws.cy; a.cz = c.ws.cz;
     a.t = t;
-    a.l1 = c.ws.l1; a.minv = c.ws.minv; a.l2 = c.ws.l2;
+    a.rec = c.ws.rec;
     a.ws = c.ws;
     const size_t smem = sizeof(double) * 14 * (size_t)a.nx;
     cudaError_t e = cudaFuncSetAttribute(setup_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -83,7 +83,7 @@ def load():
     lib.ffp_spmv.argtypes = [vp, vp, vp, vp]
     lib.ffp_apply.argtypes = [vp, vp, vp, vp]
     lib.ffp_pcg_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, P(Stats), vp]
-    lib.ffp_export.argtypes = [vp] * 10
+    lib.ffp_export.argtypes = [vp] * 11
     lib.ffp_destroy.argtypes = [vp]
     lib.ffp_destroy.restype = None
     lib.ffp_strerror.argtypes = [ctypes.c_int]
@@ -217,7 +217,7 @@ class Preconditioner:
 
     def export(self, stream=None):
         """Stored operator bands and factors as FP64 device tensors."""
-        names = ["d", "cx", "cy", "cz", "l2", "l1", "minv", "dinv"]
+        names = ["d", "cx", "cy", "cz", "l3", "l2", "l1", "minv", "dinv"]
         out = {k: torch.empty(self.n, dtype=torch.float64, device=self.workspace.device)
                for k in names}
         st = load().ffp_export(self._h, *[_ptr(out[k]) for k in names], _stream(stream))

@@ -94,7 +94,7 @@ def factors_of(P):
     ex = {k: host(v) for k, v in P.export().items()}
     n = ex["d"].size
     nan = np.full(n, np.nan)
-    return o.Factors(P.grid, ex["cz"], nan, nan, ex["l2"], nan, ex["l1"], 1.0 / ex["minv"]), ex
+    return o.Factors(P.grid, ex["l3"], nan, nan, ex["l2"], nan, ex["l1"], 1.0 / ex["minv"]), ex
 
 
 @pytest.mark.parametrize("grid", GRIDS)
