@@ -37,6 +37,7 @@ extern "C" {
 #define FFP_ERR_BREAKDOWN (-3)      /* a non-positive / non-finite pivot or diagonal in setup,
                                        or (p, Ap) <= 0 in CG */
 #define FFP_ERR_NOT_CONVERGED (-4)  /* maxit reached; x holds the last iterate */
+#define FFP_ERR_TIMEOUT (-5)        /* a bounded wait inside a kernel gave up (results unusable) */
 #define FFP_ERR_UNSUPPORTED (-6)    /* the requested option is not available */
 
 #define FFP_MAX_NX 1024             /* longest line (cells along x) the line solvers support */

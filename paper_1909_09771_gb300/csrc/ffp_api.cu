@@ -284,6 +284,7 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
             if (cudaEventElapsedTime(&a, h->ev[0], h->ev[2]) == cudaSuccess) pre_ms += a;
             if (cudaEventElapsedTime(&b2, h->ev[1], h->ev[2]) == cudaSuccess) ntd_ms += b2;
         }
+        if (host_flags(h)[FL_TIMEOUT]) { status = FFP_ERR_TIMEOUT; break; }
         if (host_flags(h)[FL_PQ]) { status = FFP_ERR_BREAKDOWN; break; }
         rr = h->host_scal[SC_RR];
         if (!std::isfinite(rr)) { status = FFP_ERR_BREAKDOWN; break; }
@@ -326,6 +327,7 @@ const char *ffp_strerror(int status) {
         case FFP_ERR_CUDA: return "CUDA runtime error";
         case FFP_ERR_BREAKDOWN: return "breakdown: non-positive pivot or (p, Ap) <= 0";
         case FFP_ERR_NOT_CONVERGED: return "not converged within maxit";
+        case FFP_ERR_TIMEOUT: return "a bounded wait in a kernel timed out";
         case FFP_ERR_UNSUPPORTED: return "unsupported option";
         default: return "unknown status";
     }

@@ -16,23 +16,28 @@
 // their couplings through shared memory behind one named barrier and both
 // solve it.  Each line is one warp-wide twisted tridiagonal solve (level 1).
 //
-// Latency hiding.  Every warp walks a fixed sequence of line steps -- per
-// plane its lower-sweep lines, the twist line, its upper-sweep lines -- and
-// all the data a step reads is known in advance, except what this kernel
-// itself writes.  At step g the warp issues the asynchronous copies of step
-// g+D into a ring of D+1 shared-memory stages and waits for step g's:
-//   * the factor line records (coupling, 1/M, l2, l3 fields and the twist cell)
-//     as 16-byte chunks shared by the warp's lanes;
-//   * the vector rows of the step (r, y of the neighbouring plane, the lower-
-//     sweep result w, ...) as one 8-byte copy per cell, each lane copying the
-//     cells it owns.
-// A vector row this kernel wrote at step g - delta is fetched only when
-// delta > D (it was written before the copy was issued, by the same lane, or
-// by lane 0 for the twist cell behind the per-step __syncwarp); rows with
-// delta <= D, which occur at the first and last lines of a plane, are loaded
-// directly when used.  The twist line's result of the previous plane, which
-// the other warp of the pair wrote, is never read back from global memory:
-// both warps keep their own copy in shared memory.
+// Latency hiding (warp specialisation).  Each of the two compute warps walks
+// a fixed sequence of line steps -- per plane its lower-sweep lines, the twist
+// line, its upper-sweep lines -- and has a producer warp (warps 2 and 3) that
+// walks the same sequence ahead of it.  The producer copies what step g reads
+// into stage g mod NST of a ring in shared memory with cp.async:
+//   * the factor line records (coupling, 1/M, l2, l3 fields and the twist
+//     cell) as 16-byte chunks shared by its lanes;
+//   * the vector rows of the step as one 8-byte copy per cell, lane l copying
+//     the cells compute lane l owns;
+// and signals the stage's "full" mbarrier when its copies complete; the
+// compute warp waits on it, computes, and releases the stage on its "empty"
+// mbarrier.  All the address arithmetic thus stays off the compute warp's
+// instruction stream.  The producer refills stage g only after the compute
+// warp released step g - NST, so a vector row the kernel wrote at step
+// g - delta can be staged when delta >= NST (release/acquire through the
+// mbarriers orders the write before the copy); rows with delta < NST occur at
+// the first lines of the lower and upper sweeps and are loaded directly.  The
+// twist line of the previous plane, which only compute warp 0 writes, is
+// never read back from global memory: both compute warps keep their own copy
+// in shared memory.  Every mbarrier wait has an iteration limit; on timeout
+// the warp records FL_TIMEOUT and runs on without waiting, so the kernel always
+// finishes (with unusable results) instead of hanging.
 #pragma once
 #include "ffp_plane.cuh"
 #include "ffp_kernels.h"
@@ -46,53 +51,86 @@ struct ApplyArgs {
     const double *r;  // right-hand side
     double *z;        // output (holds y after the lower sweeps)
     double *scr;      // 2 planes of scratch (phase 2 intermediates)
-    int nst;          // stages in the ring (D = nst - 1)
-    int vstage;       // 1: vector rows are staged too; 0: loaded directly
-    int stage_bytes;
+    int *flags;       // error flags (FL_TIMEOUT)
 };
 
-// stage layout (bytes): fields [5][32 S] F, mids [4][8] F, vectors [3][S+1][32] double
-template <int S, typename F>
-struct StageLayout {
+constexpr int kSmemBudget = 220 * 1024;
+
+// Compile-time stage layout for phase PH: fields [NF][32 S] F, twist-cell
+// blocks [NF][8] F, vectors [NV][S+1][32] double.
+template <int S, typename F, int PH>
+struct Stage {
+    using R = typename Compute<F>::type;
+    static constexpr int NF = (PH == 1) ? 5 : 4;  // eout, minv, l2, l3 (, second l3)
+    static constexpr int NM = (PH == 1) ? 4 : 3;  // twist-cell blocks: own, l2, l3 (, second l3)
+    static constexpr int NV = (PH == 1) ? 3 : 2;
     static constexpr int kFld = 32 * S * (int)sizeof(F);
     static constexpr int kMid = 8 * (int)sizeof(F);
-    static constexpr int kFields = 5 * kFld;
-    static constexpr int kMids = 4 * kMid;
+    static constexpr int kVecOff = ((NF * kFld + NM * kMid + 15) / 16) * 16;
     static constexpr int kVec = (S + 1) * 32 * 8;
-    __host__ __device__ static constexpr int bytes(int vstage) {
-        return ((kFields + kMids + 15) / 16) * 16 + (vstage ? 3 * kVec : 0);
+    // twist caches + full/empty mbarriers of both rings
+    static constexpr int kExtra = 2 * (S + 1) * 32 * (int)sizeof(R) + 2 * 2 * 5 * 8;
+    __host__ __device__ static constexpr int bytes_v(int vst) { return kVecOff + (vst ? NV * kVec : 0); }
+    __host__ __device__ static constexpr int total(int nst, int vst, int nx) {
+        return 2 * nst * bytes_v(vst) + kExtra + 4 * nx * (int)sizeof(R);
     }
-    __host__ __device__ static constexpr int vec_off() { return ((kFields + kMids + 15) / 16) * 16; }
+    // vector rows are staged if three stages of them fit beside the longest gbuf
+    static constexpr int VST = total(3, 1, FFP_MAX_NX) <= kSmemBudget ? 1 : 0;
+    __host__ __device__ static constexpr int pick() {
+        int n = 5;
+        while (n > 2 && total(n, VST, FFP_MAX_NX) > kSmemBudget) --n;
+        return n;
+    }
+    static constexpr int NST = pick();
+    static constexpr int D = NST - 1;  // a staged row must be written >= NST = D + 1 steps earlier
+    static constexpr int kBytes = bytes_v(VST);
 };
 
-// what one step reads
-struct StepPlan {
-    bool valid;
-    int kind;             // 0 lower, 1 twist, 2 upper
-    int t;                // chain position of the line in this warp's half
-    int i, k;             // plane, line
-    long own, l2r, l3a, l3b;  // record indices (-1: none)
-    const double *v[3];   // vector rows to stage (null: none)
-};
-
-template <int S, typename F>
-struct ApplyWarp {
+template <int S, typename F, int PH>
+__global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
     using R = typename Compute<F>::type;
-    using LY = StageLayout<S, F>;
-    const ApplyArgs<F> &A;
-    int phase, h, wid, lane, cnt;
-    int nl, spp, npl, my, mz, nst, D;
-    long nxy;
-    unsigned char *ring;  // this warp's stages
-    R *tcache;            // this warp's copy of the previous plane's twist line [(S+1)][32]
+    using SG = Stage<S, F, PH>;
+    constexpr int NF = SG::NF, NM = SG::NM, NV = SG::NV, NST = SG::NST, D = SG::D, VST = SG::VST;
+    static_assert(SG::total(NST, VST, FFP_MAX_NX) <= kSmemBudget, "stage ring does not fit");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool producer = warp >= 2;
+    const int wid = warp & 1;  // the level-2 half this warp computes or feeds
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const int nxy = nx * ny;
+    const LineMap L(nx);
+    const int cnt = lane_count<S>(L, lane);
+    const int h = (PH == 1) ? 0 : (int)blockIdx.x;
+    const int my = (ny - 1) / 2, mz = (nz - 1) / 2;
+    const int nl = (wid == 0) ? my : ny - 1 - my;
+    const int spp = 2 * nl + 1;
+    const int npl = (PH == 1) ? 1 : ((h == 0) ? mz : nz - 1 - mz);
+    unsigned char *ring = smem_raw + (size_t)wid * NST * SG::kBytes;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem_raw + 2 * (size_t)NST * SG::kBytes);
+    unsigned long long *full = bars + wid * 2 * 5, *empty = full + 5;
+    R *caches = reinterpret_cast<R *>(bars + 2 * 2 * 5);
+    R *tcache = caches + wid * (S + 1) * 32;
+    R *gbase = caches + 2 * (S + 1) * 32;
+    if (threadIdx.x == 0) {
+        // bars[c*10 + q] = full[q], bars[c*10 + 5 + q] = empty[q] of compute warp c
+        for (int c = 0; c < 2; ++c)
+            for (int q = 0; q < 5; ++q) {
+                mbar_init(bars + c * 10 + q, 32);     // full: one cp.async arrival per producer lane
+                mbar_init(bars + c * 10 + 5 + q, 1);  // empty: one arrival by the compute warp
+            }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool aborted = false;
+    int cell[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) cell[s] = (s < cnt) ? slot_cell<S>(L, lane, s) : 0;
+    const long RL = rec_len(S);
 
-    __device__ __forceinline__ ApplyWarp(const ApplyArgs<F> &a) : A(a) {}
-
-    // plane of chain position pl, the plane whose output it couples to, and the coupling plane
-    __device__ __forceinline__ void plane_of(int pl, int &i, int &other, int &cpl) const {
-        const int nz = A.nz;
-        if (phase == 1) { i = mz; other = -1; cpl = -1; return; }
-        if (phase == 0) {
+    // plane of chain position pl, the plane whose output it couples to (-1: none), coupling plane
+    auto plane_of = [&](int pl, int &i, int &other, int &cpl) {
+        if (PH == 1) { i = mz; other = -1; cpl = -1; return; }
+        if (PH == 0) {
             i = (h == 0) ? pl : nz - 1 - pl;
             other = (pl > 0) ? ((h == 0) ? i - 1 : i + 1) : -1;
             cpl = (h == 0) ? i - 1 : i;
@@ -102,306 +140,309 @@ struct ApplyWarp {
             other = (h == 0) ? i + 1 : i - 1;
             cpl = (h == 0) ? i : i - 1;
         }
-    }
+    };
+    auto line_of = [&](int t) { return (wid == 0) ? t : ny - 1 - t; };
 
-    __device__ __forceinline__ StepPlan plan(int g) const {
-        StepPlan p;
-        p.valid = g < spp * npl;
-        p.v[0] = p.v[1] = p.v[2] = nullptr;
-        p.own = p.l2r = p.l3a = p.l3b = -1;
-        if (!p.valid) return p;
-        const int nx = A.nx, ny = A.ny;
-        const int pl = g / spp, s = g - pl * spp;
-        int i, other, cpl;
-        plane_of(pl, i, other, cpl);
-        int t, k, kind;
-        if (s < nl) { kind = 0; t = s; k = (wid == 0) ? t : ny - 1 - t; }
-        else if (s == nl) { kind = 1; t = nl; k = my; }
-        else { kind = 2; t = 2 * nl - s; k = (wid == 0) ? t : ny - 1 - t; }
-        p.kind = kind; p.t = t; p.i = i; p.k = k;
-        p.own = (long)i * ny + k;
-        const long row = (long)i * nxy + (long)k * nx;
-        if (kind == 0) {
-            if (t > 0) p.l2r = (long)i * ny + ((wid == 0) ? k - 1 : k);
-        } else if (kind == 1) {
-            if (nl > 0) p.l2r = (long)i * ny + ((wid == 0) ? my - 1 : my);
-        } else {
-            p.l2r = (long)i * ny + ((wid == 0) ? k : k - 1);
-        }
-        const int D_ = D;
-        if (phase == 0) {
-            if (kind != 2) {
-                if (other >= 0) p.l3a = (long)cpl * ny + k;
-                p.v[0] = A.r + row;
-                if (kind == 0 && other >= 0 && 2 * t + 1 > D_) p.v[1] = A.z + (long)other * nxy + (long)k * nx;
-            } else if (2 * (nl - t) > D_) {
-                p.v[0] = A.z + row;
+    // ------------------------------------------------------------------ producer
+    // future-step cursor: chain plane fpl, step fs within the plane, global step fg
+    int fpl = 0, fs = 0, fg = 0;
+    auto issue_next = [&]() {
+        if (fpl < npl) {
+            const int slot = fg % NST, use = fg / NST;
+            if (use > 0 && !aborted && !mbar_wait(empty + slot, (use - 1) & 1)) {
+                aborted = true;
+                atomicOr(A.flags + FL_TIMEOUT, 1);
             }
-        } else if (phase == 1) {
-            if (kind != 2) {
-                p.v[0] = A.r + row;
-                if (mz > 0) { p.l3a = (long)(mz - 1) * ny + k; p.v[1] = A.z + row - nxy; }
-                if (mz < A.nz - 1) { p.l3b = (long)mz * ny + k; p.v[2] = A.z + row + nxy; }
-            } else if (2 * (nl - t) > D_) {
-                p.v[0] = A.z + row;
-            }
-        } else {
-            if (kind != 2) {
-                p.l3a = (long)cpl * ny + k;
-                // the first plane's neighbour is the twist plane, written by the previous launch
-                if (pl == 0 || (kind == 0 && 2 * t + 1 > D_))
-                    p.v[0] = A.z + (long)other * nxy + (long)k * nx;
-                if (kind == 1) p.v[1] = A.z + row;  // y_i of the twist line
+            unsigned char *st = ring + slot * SG::kBytes;
+            int i, other, cpl;
+            plane_of(fpl, i, other, cpl);
+            const int kind = (fs < nl) ? 0 : ((fs == nl) ? 1 : 2);
+            const int t = (kind == 0) ? fs : ((kind == 1) ? nl : 2 * nl - fs);
+            const int k = (kind == 1) ? my : line_of(t);
+            const long own = (long)i * ny + k;
+            long l2r = -1, l3a = -1, l3b = -1;
+            if (kind == 0) { if (t > 0) l2r = (long)i * ny + ((wid == 0) ? k - 1 : k); }
+            else if (kind == 1) { if (nl > 0) l2r = (long)i * ny + ((wid == 0) ? my - 1 : my); }
+            else l2r = (long)i * ny + ((wid == 0) ? k : k - 1);
+            const long row = (long)i * nxy + (long)k * nx;
+            const double *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;
+            if (PH == 0) {
+                if (kind != 2) {
+                    if (other >= 0) l3a = (long)cpl * ny + k;
+                    v0 = A.r + row;
+                    if (kind == 0 && other >= 0 && 2 * t + 1 > D) v1 = A.z + (long)other * nxy + (long)k * nx;
+                } else if (2 * (nl - t) > D) {
+                    v0 = A.z + row;
+                }
+            } else if (PH == 1) {
+                if (kind != 2) {
+                    v0 = A.r + row;
+                    if (mz > 0) { l3a = (long)(mz - 1) * ny + k; v1 = A.z + row - nxy; }
+                    if (mz < nz - 1) { l3b = (long)mz * ny + k; v2 = A.z + row + nxy; }
+                } else if (2 * (nl - t) > D) {
+                    v0 = A.z + row;
+                }
             } else {
-                if (2 * (nl - t) > D_) p.v[0] = A.scr + h * nxy + (long)k * nx;
-                p.v[1] = A.z + row;                 // y_i, written by phase 0/1
-            }
-        }
-        return p;
-    }
-
-    __device__ __forceinline__ unsigned char *stage(int g) const {
-        return ring + (size_t)(g % nst) * A.stage_bytes;
-    }
-
-    // issue the copies of step g into its stage and commit one group (empty past the end)
-    __device__ __forceinline__ void issue(int g) const {
-        const StepPlan p = plan(g);
-        if (p.valid) {
-            unsigned char *st = stage(g);
-            const long RL = rec_len(S);
-            const long srcs[5] = {p.own, p.own, p.l2r, p.l3a, p.l3b};
-            const int flds[5] = {REC_EOUT, REC_MINV, REC_L2, REC_L3, REC_L3};
-            constexpr int CH = LY::kFld / 16;  // 16-byte chunks per field
-#pragma unroll
-            for (int f = 0; f < 5; ++f) {
-                if (srcs[f] < 0) continue;
-                const unsigned char *src =
-                    reinterpret_cast<const unsigned char *>(A.rec + srcs[f] * RL + (long)flds[f] * 32 * S);
-                for (int c = lane; c < CH; c += 32) cp_async16(st + f * LY::kFld + c * 16, src + c * 16);
-            }
-            // twist-cell blocks of the own, l2, l3a, l3b records
-            constexpr int MC = LY::kMid / 16;
-            const long ms[4] = {p.own, p.l2r, p.l3a, p.l3b};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (ms[j] < 0) continue;
-                const unsigned char *src =
-                    reinterpret_cast<const unsigned char *>(A.rec + ms[j] * RL + (long)REC_NFIELD * 32 * S);
-                for (int c = lane; c < MC; c += 32) cp_async16(st + LY::kFields + j * LY::kMid + c * 16, src + c * 16);
-            }
-            if (A.vstage) {
-                const LineMap L(A.nx);
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    if (!p.v[v]) continue;
-                    double *dst = reinterpret_cast<double *>(st + LY::vec_off() + v * LY::kVec);
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        if (s < cnt) cp_async8(dst + s * 32 + lane, p.v[v] + slot_cell<S>(L, lane, s));
-                    cp_async8(dst + S * 32 + lane, p.v[v] + L.m);
+                if (kind != 2) {
+                    l3a = (long)cpl * ny + k;
+                    // the first plane's neighbour is the twist plane, written by the previous launch
+                    if (fpl == 0 || (kind == 0 && 2 * t + 1 > D)) v0 = A.z + (long)other * nxy + (long)k * nx;
+                    if (kind == 1) v1 = A.z + row;  // y of the twist line
+                } else {
+                    if (2 * (nl - t) > D) v0 = A.scr + (long)h * nxy + (long)k * nx;
+                    v1 = A.z + row;                 // y, written by phase 0/1
                 }
             }
-        }
-        cp_async_commit();
-    }
-
-    // staged or direct read of cell (slot s / twist cell) of vector row v of step p
-    __device__ __forceinline__ R vec(const unsigned char *st, const StepPlan &p, int v,
-                                     const double *row, int s, int a) const {
-        if (A.vstage && p.v[v]) {
-            const double *src = reinterpret_cast<const double *>(st + LY::vec_off() + v * LY::kVec);
-            return (R)src[s * 32 + lane];
-        }
-        return (R)row[a];
-    }
-
-    __device__ __forceinline__ R fld(const unsigned char *st, int f, int s) const {
-        const F *src = reinterpret_cast<const F *>(st + f * LY::kFld);
-        return to_r(src[s * 32 + lane], R());
-    }
-    __device__ __forceinline__ R mid(const unsigned char *st, int j, int which) const {
-        const F *src = reinterpret_cast<const F *>(st + LY::kFields + j * LY::kMid);
-        return to_r(src[which], R());
-    }
-
-    // factor of the step's line from the stage (ein = eout of the chain predecessor)
-    __device__ __forceinline__ void factor(const unsigned char *st, LineFactor<S, R> &f) const {
+            // record fields: [0] own eout, [1] own minv, [2] l2 row, [3] l3a, [4] l3b
+            const long src[5] = {own, own, l2r, l3a, l3b};
+            const int fld[5] = {REC_EOUT, REC_MINV, REC_L2, REC_L3, REC_L3};
+            constexpr int CH = SG::kFld / 16;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            f.eout[s] = fld(st, 0, s);
-            f.minv[s] = fld(st, 1, s);
+            for (int f = 0; f < NF; ++f) {
+                if (src[f] >= 0) {
+                    const unsigned char *gp = reinterpret_cast<const unsigned char *>(
+                        A.rec + src[f] * RL + (long)fld[f] * 32 * S);
+#pragma unroll
+                    for (int c0 = 0; c0 < CH; c0 += 32)
+                        if (c0 + lane < CH)
+                            cp_async16(st + f * SG::kFld + (c0 + lane) * 16, gp + (c0 + lane) * 16);
+                }
+            }
+            // twist-cell blocks: [0] own, [1] l2 row, [2] l3a, [3] l3b
+            constexpr int MC = SG::kMid / 16;
+            if (lane < NM * MC) {
+                const int j = lane / MC, c = lane % MC;
+                const long msrc = (j == 0) ? own : ((j == 1) ? l2r : ((j == 2) ? l3a : l3b));
+                if (msrc >= 0)
+                    cp_async16(st + NF * SG::kFld + j * SG::kMid + c * 16,
+                               reinterpret_cast<const unsigned char *>(A.rec + msrc * RL +
+                                                                       (long)REC_NFIELD * 32 * S) + c * 16);
+            }
+            if (VST) {
+                const double *vs[3] = {v0, v1, v2};
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    if (vs[v]) {
+                        double *dst = reinterpret_cast<double *>(st + SG::kVecOff + v * SG::kVec);
+#pragma unroll
+                        for (int s = 0; s < S; ++s)
+                            if (s < cnt) cp_async8(dst + s * 32 + lane, vs[v] + cell[s]);
+                        cp_async8(dst + S * 32 + lane, vs[v] + L.m);
+                    }
+                }
+            }
+            mbar_arrive_cpasync(full + slot);
         }
+        ++fg;
+        if (++fs == spp) { fs = 0; ++fpl; }
+    };
+    if (producer) {
+        const int total = spp * npl;
+        for (int q = 0; q < total; ++q) issue_next();
+        cp_async_wait<0>();
+        return;
+    }
+
+    // stage accessors
+    auto F_ = [&](const unsigned char *st, int f, int s) -> R {
+        return to_r(reinterpret_cast<const F *>(st + f * SG::kFld)[s * 32 + lane], R());
+    };
+    auto M_ = [&](const unsigned char *st, int j, int w) -> R {
+        return to_r(reinterpret_cast<const F *>(st + NF * SG::kFld + j * SG::kMid)[w], R());
+    };
+    auto V_ = [&](const unsigned char *st, int v, int s) -> R {
+        return (R)reinterpret_cast<const double *>(st + SG::kVecOff + v * SG::kVec)[s * 32 + lane];
+    };
+    auto factor = [&](const unsigned char *st, LineFactor<S, R> &f) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) { f.eout[s] = F_(st, 0, s); f.minv[s] = F_(st, 1, s); }
         const R prev = __shfl_up_sync(0xffffffffu, f.eout[S - 1], 1, 16);
 #pragma unroll
         for (int s = S - 1; s > 0; --s) f.ein[s] = f.eout[s - 1];
         f.ein[0] = ((lane & 15) == 0) ? R(0) : prev;
-        f.minv_m = mid(st, 0, MID_MINV);
-        f.em1 = mid(st, 0, MID_EM1);
-        f.em = mid(st, 0, MID_EM);
-    }
-};
+        f.minv_m = M_(st, 0, MID_MINV);
+        f.em1 = M_(st, 0, MID_EM1);
+        f.em = M_(st, 0, MID_EM);
+    };
 
-template <int S, typename F>
-__global__ void __launch_bounds__(64) apply_kernel(ApplyArgs<F> A, int phase) {
-    using R = typename Compute<F>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nx = A.nx, ny = A.ny, nz = A.nz;
-    const LineMap L(nx);
-    const long nxy = (long)nx * ny;
-    // shared memory: [2 warps][nst stages] | twist caches [2][S+1][32] R | gbuf [2 parity][2][nx] R
-    const size_t ring_bytes = (size_t)A.nst * A.stage_bytes;
-    R *tc = reinterpret_cast<R *>(smem_raw + 2 * ring_bytes);
-    R *gbase = tc + 2 * (S + 1) * 32;
-    ApplyWarp<S, F> W(A);
-    W.phase = phase; W.h = (phase == 1) ? 0 : blockIdx.x; W.wid = wid; W.lane = lane;
-    W.cnt = lane_count<S>(L, lane);
-    W.my = (ny - 1) / 2; W.mz = (nz - 1) / 2; W.nxy = nxy;
-    W.nl = (wid == 0) ? W.my : ny - 1 - W.my;
-    W.spp = 2 * W.nl + 1;
-    W.npl = (phase == 1) ? 1 : ((blockIdx.x == 0) ? W.mz : nz - 1 - W.mz);
-    W.nst = A.nst; W.D = A.nst - 1;
-    W.ring = smem_raw + wid * ring_bytes;
-    W.tcache = tc + wid * (S + 1) * 32;
-    const int cnt = W.cnt, D = W.D, nl = W.nl, my = W.my;
-    for (int g = 0; g < D; ++g) W.issue(g);
-
-    R w[S], wm = R(0);   // previous lower-sweep line (lower sweep), then u of the line towards my
+    // ------------------------------------------------------------------ compute
+    R w[S], wm = R(0);
+#pragma unroll
+    for (int s = 0; s < S; ++s) w[s] = R(0);
     int g = 0;
-    for (int pl = 0; pl < W.npl; ++pl) {
+    // begin a step: wait until step g's stage is full
+    auto begin = [&]() -> const unsigned char * {
+        const int slot = g % NST;
+        if (!aborted && !mbar_wait(full + slot, (g / NST) & 1)) {
+            aborted = true;
+            atomicOr(A.flags + FL_TIMEOUT, 1);
+        }
+        return ring + slot * SG::kBytes;
+    };
+    // end a step: release step g's stage to the producer
+    auto finish = [&]() {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + g % NST);
+    };
+
+    for (int pl = 0; pl < npl; ++pl) {
         int i, other, cpl;
-        W.plane_of(pl, i, other, cpl);
+        plane_of(pl, i, other, cpl);
         R *gbuf = gbase + (pl & 1) * 2 * nx;
         const long pbase = (long)i * nxy;
-        for (int s = 0; s < W.spp; ++s, ++g) {
-            __syncwarp();
-            W.issue(g + D);
-            cp_async_wait_dyn(D);
-            __syncwarp();
-            const unsigned char *st = W.stage(g);
-            const StepPlan p = W.plan(g);
+        const double *zo = (other >= 0) ? A.z + (long)other * nxy : A.z;
+        double *scrp = A.scr + (long)h * nxy;
+        // ------------------------------------------------------------ lower sweep
+        for (int t = 0; t < nl; ++t, ++g) {
+            const unsigned char *st = begin();
+            const int k = line_of(t);
+            const long row = pbase + (long)k * nx;
             LineFactor<S, R> f;
-            W.factor(st, f);
-            const long row = pbase + (long)p.k * nx;
-            R b[S], bm;
-            // ---------------------------------------------------------- rhs of the step
-            if (p.kind != 2) {
-                // plane right-hand side v of this line
+            factor(st, f);
+            const bool far = 2 * t + 1 > D;
+            R b[S], bm = R(0);
 #pragma unroll
-                for (int q = 0; q <= S; ++q) {
-                    const int sidx = (q < S) ? q : S;
-                    if (q < S && q >= cnt) { b[q] = R(0); continue; }
-                    const int a = (q < S) ? slot_cell<S>(L, lane, q) : L.m;
-                    R v;
-                    if (phase == 0) {
-                        v = W.vec(st, p, 0, A.r + row, sidx, a);
+            for (int s = 0; s <= S; ++s) {
+                const bool in = (s == S) || (s < cnt);
+                const int a = (s == S) ? L.m : cell[s];
+                R v = R(0);
+                if (in) {
+                    const R c3 = (s < S) ? F_(st, 3, s) : M_(st, 2, MID_L3);
+                    if (PH == 0) {
+                        v = VST ? V_(st, 0, s) : (R)A.r[row + a];
                         if (other >= 0) {
-                            R yp;
-                            if (p.kind == 1) yp = W.tcache[sidx * 32 + lane];
-                            else yp = W.vec(st, p, 1, A.z + (long)other * nxy + (long)p.k * nx, sidx, a);
-                            const R c3 = (q < S) ? W.fld(st, 3, q) : W.mid(st, 2, MID_L3);
+                            const R yp = (VST && far) ? V_(st, 1, s) : (R)zo[(long)k * nx + a];
                             v -= c3 * yp;
                         }
-                    } else if (phase == 1) {
-                        v = W.vec(st, p, 0, A.r + row, sidx, a);
-                        if (W.mz > 0) {
-                            const R c3 = (q < S) ? W.fld(st, 3, q) : W.mid(st, 2, MID_L3);
-                            v -= c3 * W.vec(st, p, 1, A.z + row - nxy, sidx, a);
-                        }
-                        if (W.mz < nz - 1) {
-                            const R c3 = (q < S) ? W.fld(st, 4, q) : W.mid(st, 3, MID_L3);
-                            v -= c3 * W.vec(st, p, 2, A.z + row + nxy, sidx, a);
+                    } else if (PH == 1) {
+                        v = VST ? V_(st, 0, s) : (R)A.r[row + a];
+                        if (mz > 0) v -= c3 * (VST ? V_(st, 1, s) : (R)A.z[row - nxy + a]);
+                        if (mz < nz - 1) {
+                            const R c4 = (s < S) ? F_(st, 4, s) : M_(st, 3, MID_L3);
+                            v -= c4 * (VST ? V_(st, 2, s) : (R)A.z[row + nxy + a]);
                         }
                     } else {
-                        R za;
-                        if (p.kind == 1 && pl > 0) za = W.tcache[sidx * 32 + lane];
-                        else za = W.vec(st, p, 0, A.z + (long)other * nxy + (long)p.k * nx, sidx, a);
-                        const R c3 = (q < S) ? W.fld(st, 3, q) : W.mid(st, 2, MID_L3);
+                        const R za = (VST && (far || pl == 0)) ? V_(st, 0, s) : (R)zo[(long)k * nx + a];
                         v = c3 * za;
                     }
-                    if (q < S) b[q] = v; else bm = v;
+                    if (t > 0) v -= ((s < S) ? F_(st, 2, s) : M_(st, 1, MID_L2)) * ((s < S) ? w[s] : wm);
                 }
-                if (p.kind == 0 && p.t > 0) {
-#pragma unroll
-                    for (int q = 0; q < S; ++q) b[q] -= W.fld(st, 2, q) * w[q];
-                    bm -= W.mid(st, 1, MID_L2) * wm;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < S; ++q) b[q] = W.fld(st, 2, q) * w[q];
-                bm = W.mid(st, 1, MID_L2) * wm;
+                if (s < S) b[s] = v; else bm = v;
             }
-            if (p.kind == 1) {
-                // couplings of the two halves into the twist line (Algorithm 2, steps 9-11)
-                R *gw = gbuf + wid * nx;
-#pragma unroll
-                for (int q = 0; q < S; ++q)
-                    if (q < cnt) gw[slot_cell<S>(L, lane, q)] = (nl > 0) ? W.fld(st, 2, q) * w[q] : R(0);
-                if (lane == 0) gw[L.m] = (nl > 0) ? W.mid(st, 1, MID_L2) * wm : R(0);
-                named_barrier(1, 64);
-#pragma unroll
-                for (int q = 0; q < S; ++q)
-                    if (q < cnt) {
-                        const int a = slot_cell<S>(L, lane, q);
-                        b[q] = b[q] - gbuf[a] - gbuf[nx + a];
-                    }
-                bm = bm - gbuf[L.m] - gbuf[nx + L.m];
-            }
-            // ---------------------------------------------------------- line solve
             R x[S], xm;
-            twisted_solve<S, R>(f, cnt, lane, b, bm, x, xm);
-            // ---------------------------------------------------------- results
-            if (p.kind == 0) {
-                double *out = (phase == 2) ? A.scr + W.h * nxy + (long)p.k * nx : A.z + row;
+            twisted_solve_fast<S, R>(f, cnt, lane, b, bm, x, xm);
+            double *out = (PH == 2) ? scrp + (long)k * nx : A.z + row;
 #pragma unroll
-                for (int q = 0; q < S; ++q)
-                    if (q < cnt) out[slot_cell<S>(L, lane, q)] = (double)x[q];
-                if (lane == 0) out[L.m] = (double)xm;
-#pragma unroll
-                for (int q = 0; q < S; ++q) w[q] = x[q];
-                wm = xm;
-            } else if (p.kind == 1) {
-                // twist line: u_my (kept in registers for the upper sweep)
-#pragma unroll
-                for (int q = 0; q <= S; ++q) {
-                    if (q < S && q >= cnt) continue;
-                    const int sidx = (q < S) ? q : S;
-                    const int a = (q < S) ? slot_cell<S>(L, lane, q) : L.m;
-                    const R u = (q < S) ? x[q] : xm;
-                    R fin = u;
-                    if (phase == 2) fin = W.vec(st, p, 1, A.z + row, sidx, a) - u;
-                    W.tcache[sidx * 32 + lane] = fin;
-                    if (wid == 0 && (q < S || lane == 0)) A.z[row + a] = (double)fin;
-                }
-#pragma unroll
-                for (int q = 0; q < S; ++q) w[q] = x[q];
-                wm = xm;
-            } else {
-                const double *wrow = (phase == 2) ? A.scr + W.h * nxy + (long)p.k * nx : A.z + row;
-#pragma unroll
-                for (int q = 0; q <= S; ++q) {
-                    if (q < S && q >= cnt) continue;
-                    const int sidx = (q < S) ? q : S;
-                    const int a = (q < S) ? slot_cell<S>(L, lane, q) : L.m;
-                    const R u = W.vec(st, p, 0, wrow, sidx, a) - ((q < S) ? x[q] : xm);
-                    R fin = u;
-                    if (phase == 2) fin = W.vec(st, p, 1, A.z + row, sidx, a) - u;
-                    if (q < S || lane == 0) A.z[row + a] = (double)fin;
-                    if (q < S) w[q] = u; else wm = u;
-                }
+            for (int s = 0; s < S; ++s) {
+                if (s < cnt) out[cell[s]] = (double)x[s];
+                w[s] = x[s];
             }
+            if (lane == 0) out[L.m] = (double)xm;
+            wm = xm;
+            finish();
+        }
+        // ------------------------------------------------------------ twist line
+        R u[S], um;
+        {
+            const unsigned char *st = begin();
+            const long row = pbase + (long)my * nx;
+            LineFactor<S, R> f;
+            factor(st, f);
+            R *gw = gbuf + wid * nx;
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                if (s < cnt) gw[cell[s]] = (nl > 0) ? F_(st, 2, s) * w[s] : R(0);
+            if (lane == 0) gw[L.m] = (nl > 0) ? M_(st, 1, MID_L2) * wm : R(0);
+            R b[S], bm = R(0);
+#pragma unroll
+            for (int s = 0; s <= S; ++s) {
+                const bool in = (s == S) || (s < cnt);
+                const int a = (s == S) ? L.m : cell[s];
+                R v = R(0);
+                if (in) {
+                    const R c3 = (s < S) ? F_(st, 3, s) : M_(st, 2, MID_L3);
+                    if (PH == 0) {
+                        v = VST ? V_(st, 0, s) : (R)A.r[row + a];
+                        if (other >= 0) v -= c3 * tcache[s * 32 + lane];
+                    } else if (PH == 1) {
+                        v = VST ? V_(st, 0, s) : (R)A.r[row + a];
+                        if (mz > 0) v -= c3 * (VST ? V_(st, 1, s) : (R)A.z[row - nxy + a]);
+                        if (mz < nz - 1) {
+                            const R c4 = (s < S) ? F_(st, 4, s) : M_(st, 3, MID_L3);
+                            v -= c4 * (VST ? V_(st, 2, s) : (R)A.z[row + nxy + a]);
+                        }
+                    } else {
+                        const R za = (pl == 0) ? (VST ? V_(st, 0, s) : (R)zo[(long)my * nx + a])
+                                               : tcache[s * 32 + lane];
+                        v = c3 * za;
+                    }
+                }
+                if (s < S) b[s] = v; else bm = v;
+            }
+            named_barrier(1, 64);
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                if (s < cnt) b[s] = b[s] - gbuf[cell[s]] - gbuf[nx + cell[s]];
+            bm = bm - gbuf[L.m] - gbuf[nx + L.m];
+            twisted_solve_fast<S, R>(f, cnt, lane, b, bm, u, um);
+            // final value of the twist line: u (phases 0, 1) or y - u (phase 2)
+#pragma unroll
+            for (int s = 0; s <= S; ++s) {
+                const bool in = (s == S) || (s < cnt);
+                if (!in) continue;
+                const int a = (s == S) ? L.m : cell[s];
+                const R uu = (s < S) ? u[s] : um;
+                R fin = uu;
+                if (PH == 2) fin = (VST ? V_(st, 1, s) : (R)A.z[row + a]) - uu;
+                tcache[s * 32 + lane] = fin;
+                if (wid == 0 && (s < S || lane == 0)) A.z[row + a] = (double)fin;
+            }
+            finish();
+            ++g;
+        }
+        // ------------------------------------------------------------ upper sweep
+        for (int t = nl - 1; t >= 0; --t, ++g) {
+            const unsigned char *st = begin();
+            const int k = line_of(t);
+            const long row = pbase + (long)k * nx;
+            LineFactor<S, R> f;
+            factor(st, f);
+            const bool far = 2 * (nl - t) > D;
+            R b[S], bm;
+#pragma unroll
+            for (int s = 0; s < S; ++s) b[s] = F_(st, 2, s) * u[s];
+            bm = M_(st, 1, MID_L2) * um;
+            R x[S], xm;
+            twisted_solve_fast<S, R>(f, cnt, lane, b, bm, x, xm);
+            const double *wrow = (PH == 2) ? scrp + (long)k * nx : A.z + row;
+#pragma unroll
+            for (int s = 0; s <= S; ++s) {
+                const bool in = (s == S) || (s < cnt);
+                const int a = (s == S) ? L.m : cell[s];
+                R uu = R(0);
+                if (in) {
+                    const R wv = (VST && far) ? V_(st, 0, s) : (R)wrow[a];
+                    uu = wv - ((s < S) ? x[s] : xm);
+                    R fin = uu;
+                    if (PH == 2) fin = (VST ? V_(st, 1, s) : (R)A.z[row + a]) - uu;
+                    if (s < S || lane == 0) A.z[row + a] = (double)fin;
+                }
+                if (s < S) u[s] = uu; else um = uu;
+            }
+            finish();
         }
     }
-    cp_async_wait<0>();
 }
 
-// shared memory the kernel needs for nst stages
-template <int S, typename F>
-static size_t apply_smem(int nx, int nst, int vstage) {
-    using R = typename Compute<F>::type;
-    return 2 * (size_t)nst * StageLayout<S, F>::bytes(vstage) + 2 * (S + 1) * 32 * sizeof(R) +
-           4 * (size_t)nx * sizeof(R);
+template <int S, typename F, int PH>
+static cudaError_t launch_phase(const ApplyArgs<F> &a, int grid, cudaStream_t st) {
+    using SG = Stage<S, F, PH>;
+    const size_t smem = (size_t)SG::total(SG::NST, SG::VST, a.nx);
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel<S, F, PH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    apply_kernel<S, F, PH><<<grid, 128, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <int S, typename F>
@@ -410,26 +451,14 @@ cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cuda
     a.nx = c.nx; a.ny = c.ny; a.nz = c.nz;
     a.rec = (const F *)c.ws.rec;
     a.r = r; a.z = z; a.scr = c.ws.ascr;
-    // deepest ring (up to 5 stages) that fits 220 KB; drop vector staging if 2 do not fit
-    const size_t limit = 220 * 1024;
-    int vstage = 1, nst = 5;
-    while (nst > 2 && apply_smem<S, F>(c.nx, nst, vstage) > limit) --nst;
-    if (apply_smem<S, F>(c.nx, nst, vstage) > limit) { vstage = 0; nst = 5; }
-    while (nst > 2 && apply_smem<S, F>(c.nx, nst, vstage) > limit) --nst;
-    if (apply_smem<S, F>(c.nx, nst, vstage) > limit) return cudaErrorInvalidConfiguration;
-    a.nst = nst;
-    a.vstage = vstage;
-    a.stage_bytes = StageLayout<S, F>::bytes(vstage);
-    const size_t smem = apply_smem<S, F>(c.nx, nst, vstage);
-    cudaError_t e = cudaFuncSetAttribute(apply_kernel<S, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    a.flags = c.ws.flags;
     const int mz = (a.nz - 1) / 2;
     const bool halves = (mz > 0) || (a.nz - 1 - mz > 0);
-    if (halves) apply_kernel<S, F><<<2, 64, smem, st>>>(a, 0);
-    apply_kernel<S, F><<<1, 64, smem, st>>>(a, 1);
-    if (halves) apply_kernel<S, F><<<2, 64, smem, st>>>(a, 2);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (halves) e = launch_phase<S, F, 0>(a, 2, st);
+    if (e == cudaSuccess) e = launch_phase<S, F, 1>(a, 1, st);
+    if (e == cudaSuccess && halves) e = launch_phase<S, F, 2>(a, 2, st);
+    return e;
 }
 
 }  // namespace ffp

@@ -176,6 +176,74 @@ __device__ __forceinline__ void twisted_solve(const LineFactor<S, R> &f, int cnt
     xm = ym;
 }
 
+// Same solve, re-associated for a short critical path (used by the apply).
+// Forward: lane-local prefixes y[s] = pa[s] * c + pb[s] of the affine chain,
+// with c the value entering the lane.  Backward: x[s] = Xb[s] + Xa[s] * c +
+// Gs[s] * cin, where Xb, Xa, Gs are the lane-local suffix compositions of
+// x[s] = y[s] + ga[s] x[s+1] applied to pb, pa and 1, and cin the value
+// entering from the lane above.  Xb only needs pb and Xa, Gs only factors, so
+// all three are formed while the forward scan runs; the critical path is
+// forward compose -> forward scan -> backward scan -> one FMA per slot.
+template <int S, typename R>
+__device__ __forceinline__ void twisted_solve_fast(const LineFactor<S, R> &f, int cnt, int lane,
+                                                   const R (&b)[S], R bm, R (&x)[S], R &xm) {
+    const int j = lane & 15;
+    const unsigned FULL = 0xffffffffu;
+    R pa[S], pb[S], ga[S];
+    R A = R(1), B = R(0);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const bool v = s < cnt;
+        const R a_ = v ? -f.minv[s] * f.ein[s] : R(1);
+        const R be = v ? f.minv[s] * b[s] : R(0);
+        B = fma(a_, B, be);
+        A = A * a_;
+        pa[s] = A;
+        pb[s] = B;
+        ga[s] = v ? -f.minv[s] * f.eout[s] : R(1);
+    }
+    // suffix compositions of the backward chain (pads: ga = 1 and no own term)
+    R Xa[S], Xb[S], Gs[S];
+    {
+        R xa = R(0), xb = R(0), gs = R(1);
+#pragma unroll
+        for (int s = S - 1; s >= 0; --s) {
+            const bool v = s < cnt;
+            xa = fma(ga[s], xa, v ? pa[s] : R(0));
+            xb = fma(ga[s], xb, v ? pb[s] : R(0));
+            gs = ga[s] * gs;
+            Xa[s] = xa; Xb[s] = xb; Gs[s] = gs;
+        }
+    }
+    // forward scan over the 16 lanes of the chain
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const R Au = __shfl_up_sync(FULL, A, d, 16);
+        const R Bu = __shfl_up_sync(FULL, B, d, 16);
+        if (j >= d) { B = fma(A, Bu, B); A = A * Au; }
+    }
+    R c = __shfl_up_sync(FULL, B, 1, 16);
+    if (j == 0) c = R(0);
+    const R ytop = __shfl_sync(FULL, B, 15);
+    const R ybot = __shfl_sync(FULL, B, 31);
+    // backward scan: lane map x_first = G * x_in + Bb
+    R G = Gs[0];
+    R Bb = fma(Xa[0], c, Xb[0]);
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const R Gd = __shfl_down_sync(FULL, G, d, 16);
+        const R Bd = __shfl_down_sync(FULL, Bb, d, 16);
+        if (j + d < 16) { Bb = fma(G, Bd, Bb); G = G * Gd; }
+    }
+    const R ym = f.minv_m * (bm - f.em1 * ytop - f.em * ybot);
+    const R Gn = __shfl_down_sync(FULL, G, 1, 16);
+    const R Bn = __shfl_down_sync(FULL, Bb, 1, 16);
+    const R cin = (j == 15) ? ym : fma(Gn, ym, Bn);
+#pragma unroll
+    for (int s = 0; s < S; ++s) x[s] = fma(Gs[s], cin, fma(Xa[s], c, Xb[s]));
+    xm = ym;
+}
+
 // ---------------------------------------------------------------- level-1 pivots
 // Twisted pivots of the tridiagonal T (recurrence for M_i, Sec. II-A):
 // M[c] = D[c] - ein[c]^2 / M[c-1] along each chain, and at the twist cell
@@ -288,15 +356,19 @@ __host__ __device__ __forceinline__ long rec_cell(int nx, int S, int f, int midf
 }
 
 // ---------------------------------------------------------------- async copies
+// The copies carry no compiler memory clobber so that they interleave with the
+// arithmetic that follows them; cp_async_wait (which has one) orders the reads
+// of the destination after completion, and callers never read a stage that
+// copies are still being issued into.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void cp_async_wait_dyn(int n) {
@@ -308,6 +380,39 @@ __device__ __forceinline__ void cp_async_wait_dyn(int n) {
         case 4: cp_async_wait<4>(); break;
         default: cp_async_wait<5>(); break;
     }
+}
+
+// ---------------------------------------------------------------- mbarriers
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// arrive (release at CTA scope)
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// arrive when all of this thread's earlier cp.async copies have completed (count not incremented)
+__device__ __forceinline__ void mbar_arrive_cpasync(unsigned long long *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// One bounded try of the phase with the given parity (acquire at CTA scope).
+__device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Wait for a phase with an iteration limit: returns false (and the caller
+// records a timeout) if the phase does not complete in kWaitTries tries.
+constexpr unsigned kWaitTries = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    for (unsigned it = 0; it < kWaitTries; ++it)
+        if (mbar_try(bar, parity)) return true;
+    return false;
 }
 
 // ---------------------------------------------------------------- misc
@@ -373,6 +478,6 @@ enum {
     SC_TRR = 8,    // ||b - A x||^2
 };
 // flag slots
-enum { FL_BREAKDOWN = 0, FL_ARG = 1, FL_PQ = 2 };
+enum { FL_BREAKDOWN = 0, FL_ARG = 1, FL_PQ = 2, FL_TIMEOUT = 3 };
 
 }  // namespace ffp

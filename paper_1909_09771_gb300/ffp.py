@@ -22,6 +22,7 @@ FFP_ERR_ARG = -1
 FFP_ERR_CUDA = -2
 FFP_ERR_BREAKDOWN = -3
 FFP_ERR_NOT_CONVERGED = -4
+FFP_ERR_TIMEOUT = -5
 FFP_ERR_UNSUPPORTED = -6
 FFP_MAX_NX = 1024
 
