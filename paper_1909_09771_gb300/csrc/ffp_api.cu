@@ -63,6 +63,7 @@ size_t carve(const ffp_grid *g, int prec, char *base, Ws *ws) {
     w.r = (double *)take(8 * n); w.z = (double *)take(8 * n);
     w.p = (double *)take(8 * n); w.q = (double *)take(8 * n);
     w.c1 = (double *)take(8 * n); w.c2 = (double *)take(8 * n);
+    if (prec != FFP_FP64) { w.r32 = (float *)take(4 * n); w.z32 = (float *)take(4 * n); }
     w.ascr = (double *)take(8 * 2 * nxy);
     for (int h = 0; h < 2; ++h) {
         for (int pp = 0; pp < 2; ++pp)
@@ -86,7 +87,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? FFP_OK : FFP_ERR_CUDA
 // kernels launched by one B_NTD apply / one ILU(0) solve
 long long ntd_launches(const KernelCtx &c) {
     const int mz = (c.nz - 1) / 2;
-    return (mz > 0 || c.nz - 1 - mz > 0) ? 3 : 1;
+    return ((mz > 0 || c.nz - 1 - mz > 0) ? 3 : 1) + (c.prec != FFP_FP64 ? 2 : 0);
 }
 long long ilu_launches(const KernelCtx &c) { return 2LL * (c.ny + c.nz - 1); }
 

@@ -44,20 +44,30 @@
 
 namespace ffp {
 
+// Vectors are in the compute type R: FP64 for FP64 factors, FP32 otherwise
+// (the FP32 apply converts r to FP32 and z back to FP64 in GPU-wide kernels
+// around the sweeps, so no FP64 arithmetic or conversion runs inside them).
 template <typename F>
 struct ApplyArgs {
+    using R = typename Compute<F>::type;
     int nx, ny, nz;
-    const F *rec;     // factor line records
-    const double *r;  // right-hand side
-    double *z;        // output (holds y after the lower sweeps)
-    double *scr;      // 2 planes of scratch (phase 2 intermediates)
-    int *flags;       // error flags (FL_TIMEOUT)
+    const F *rec;  // factor line records
+    const R *r;    // right-hand side
+    R *z;          // output (holds y after the lower sweeps)
+    R *scr;        // 2 planes of scratch (phase 2 intermediates)
+    int *flags;    // error flags (FL_TIMEOUT)
 };
+
+__device__ __forceinline__ void cp_async_elem(float *dst, const float *src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src));
+}
+__device__ __forceinline__ void cp_async_elem(double *dst, const double *src) { cp_async8(dst, src); }
 
 constexpr int kSmemBudget = 220 * 1024;
 
 // Compile-time stage layout for phase PH: fields [NF][32 S] F, twist-cell
-// blocks [NF][8] F, vectors [NV][S+1][32] double.
+// blocks [NM][8] F, vectors [NV][S+1][32] R.
 template <int S, typename F, int PH>
 struct Stage {
     using R = typename Compute<F>::type;
@@ -67,7 +77,7 @@ struct Stage {
     static constexpr int kFld = 32 * S * (int)sizeof(F);
     static constexpr int kMid = 8 * (int)sizeof(F);
     static constexpr int kVecOff = ((NF * kFld + NM * kMid + 15) / 16) * 16;
-    static constexpr int kVec = (S + 1) * 32 * 8;
+    static constexpr int kVec = (S + 1) * 32 * (int)sizeof(R);
     // twist caches + full/empty mbarriers of both rings
     static constexpr int kExtra = 2 * (S + 1) * 32 * (int)sizeof(R) + 2 * 2 * 5 * 8;
     __host__ __device__ static constexpr int bytes_v(int vst) { return kVecOff + (vst ? NV * kVec : 0); }
@@ -165,7 +175,7 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
             else if (kind == 1) { if (nl > 0) l2r = (long)i * ny + ((wid == 0) ? my - 1 : my); }
             else l2r = (long)i * ny + ((wid == 0) ? k : k - 1);
             const long row = (long)i * nxy + (long)k * nx;
-            const double *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;
+            const R *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;
             if (PH == 0) {
                 if (kind != 2) {
                     if (other >= 0) l3a = (long)cpl * ny + k;
@@ -219,15 +229,15 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
                                                                        (long)REC_NFIELD * 32 * S) + c * 16);
             }
             if (VST) {
-                const double *vs[3] = {v0, v1, v2};
+                const R *vs[3] = {v0, v1, v2};
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if (vs[v]) {
-                        double *dst = reinterpret_cast<double *>(st + SG::kVecOff + v * SG::kVec);
+                        R *dst = reinterpret_cast<R *>(st + SG::kVecOff + v * SG::kVec);
 #pragma unroll
                         for (int s = 0; s < S; ++s)
-                            if (s < cnt) cp_async8(dst + s * 32 + lane, vs[v] + cell[s]);
-                        cp_async8(dst + S * 32 + lane, vs[v] + L.m);
+                            if (s < cnt) cp_async_elem(dst + s * 32 + lane, vs[v] + cell[s]);
+                        cp_async_elem(dst + S * 32 + lane, vs[v] + L.m);
                     }
                 }
             }
@@ -251,7 +261,7 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
         return to_r(reinterpret_cast<const F *>(st + NF * SG::kFld + j * SG::kMid)[w], R());
     };
     auto V_ = [&](const unsigned char *st, int v, int s) -> R {
-        return (R)reinterpret_cast<const double *>(st + SG::kVecOff + v * SG::kVec)[s * 32 + lane];
+        return reinterpret_cast<const R *>(st + SG::kVecOff + v * SG::kVec)[s * 32 + lane];
     };
     auto factor = [&](const unsigned char *st, LineFactor<S, R> &f) {
 #pragma unroll
@@ -290,8 +300,8 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
         plane_of(pl, i, other, cpl);
         R *gbuf = gbase + (pl & 1) * 2 * nx;
         const long pbase = (long)i * nxy;
-        const double *zo = (other >= 0) ? A.z + (long)other * nxy : A.z;
-        double *scrp = A.scr + (long)h * nxy;
+        const R *zo = (other >= 0) ? A.z + (long)other * nxy : A.z;
+        R *scrp = A.scr + (long)h * nxy;
         // ------------------------------------------------------------ lower sweep
         for (int t = 0; t < nl; ++t, ++g) {
             const unsigned char *st = begin();
@@ -331,13 +341,13 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
             }
             R x[S], xm;
             twisted_solve_fast<S, R>(f, cnt, lane, b, bm, x, xm);
-            double *out = (PH == 2) ? scrp + (long)k * nx : A.z + row;
+            R *out = (PH == 2) ? scrp + (long)k * nx : A.z + row;
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                if (s < cnt) out[cell[s]] = (double)x[s];
+                if (s < cnt) out[cell[s]] = x[s];
                 w[s] = x[s];
             }
-            if (lane == 0) out[L.m] = (double)xm;
+            if (lane == 0) out[L.m] = xm;
             wm = xm;
             finish();
         }
@@ -395,7 +405,7 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
                 R fin = uu;
                 if (PH == 2) fin = (VST ? V_(st, 1, s) : (R)A.z[row + a]) - uu;
                 tcache[s * 32 + lane] = fin;
-                if (wid == 0 && (s < S || lane == 0)) A.z[row + a] = (double)fin;
+                if (wid == 0 && (s < S || lane == 0)) A.z[row + a] = fin;
             }
             finish();
             ++g;
@@ -414,7 +424,7 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
             bm = M_(st, 1, MID_L2) * um;
             R x[S], xm;
             twisted_solve_fast<S, R>(f, cnt, lane, b, bm, x, xm);
-            const double *wrow = (PH == 2) ? scrp + (long)k * nx : A.z + row;
+            const R *wrow = (PH == 2) ? scrp + (long)k * nx : A.z + row;
 #pragma unroll
             for (int s = 0; s <= S; ++s) {
                 const bool in = (s == S) || (s < cnt);
@@ -425,7 +435,7 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
                     uu = wv - ((s < S) ? x[s] : xm);
                     R fin = uu;
                     if (PH == 2) fin = (VST ? V_(st, 1, s) : (R)A.z[row + a]) - uu;
-                    if (s < S || lane == 0) A.z[row + a] = (double)fin;
+                    if (s < S || lane == 0) A.z[row + a] = fin;
                 }
                 if (s < S) u[s] = uu; else um = uu;
             }
@@ -447,17 +457,29 @@ static cudaError_t launch_phase(const ApplyArgs<F> &a, int grid, cudaStream_t st
 
 template <int S, typename F>
 cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cudaStream_t st) {
+    using R = typename Compute<F>::type;
     ApplyArgs<F> a;
     a.nx = c.nx; a.ny = c.ny; a.nz = c.nz;
     a.rec = (const F *)c.ws.rec;
-    a.r = r; a.z = z; a.scr = c.ws.ascr;
+    a.scr = reinterpret_cast<R *>(c.ws.ascr);
     a.flags = c.ws.flags;
+    cudaError_t e = cudaSuccess;
+    if constexpr (sizeof(R) == 8) {
+        a.r = reinterpret_cast<const R *>(r);
+        a.z = reinterpret_cast<R *>(z);
+    } else {
+        a.r = reinterpret_cast<const R *>(c.ws.r32);
+        a.z = reinterpret_cast<R *>(c.ws.z32);
+        e = launch_to_f32(c, r, c.ws.r32, st);
+    }
     const int mz = (a.nz - 1) / 2;
     const bool halves = (mz > 0) || (a.nz - 1 - mz > 0);
-    cudaError_t e = cudaSuccess;
-    if (halves) e = launch_phase<S, F, 0>(a, 2, st);
+    if (e == cudaSuccess && halves) e = launch_phase<S, F, 0>(a, 2, st);
     if (e == cudaSuccess) e = launch_phase<S, F, 1>(a, 1, st);
     if (e == cudaSuccess && halves) e = launch_phase<S, F, 2>(a, 2, st);
+    if constexpr (sizeof(R) == 4) {
+        if (e == cudaSuccess) e = launch_from_f32(c, c.ws.z32, z, st);
+    }
     return e;
 }
 

@@ -447,6 +447,8 @@ struct Ws {
     double *c1, *c2;
     // CG vectors
     double *r, *z, *p, *q;
+    // FP32 copies of the apply's input and output (FP32/BF16 factors only)
+    float *r32, *z32;
     // apply scratch: 2 planes (one per level-3 half) of FP64
     double *ascr;
     // setup scratch, per half h: P bands ping-pong [h][pp][3], FP64 line factors of the

@@ -26,6 +26,8 @@ cudaError_t launch_convert_bands(const KernelCtx &c, cudaStream_t st);  // l3 (a
 cudaError_t launch_resid_vec(const KernelCtx &c, const double *r, const double *y, double *w,
                              cudaStream_t st);                           // w = r - A y
 cudaError_t launch_add(const KernelCtx &c, double *z, const double *y, cudaStream_t st);  // z += y
+cudaError_t launch_to_f32(const KernelCtx &c, const double *x, float *y, cudaStream_t st);
+cudaError_t launch_from_f32(const KernelCtx &c, const float *x, double *y, cudaStream_t st);
 cudaError_t launch_spmv(const KernelCtx &c, const double *x, double *y, cudaStream_t st);
 cudaError_t launch_export(const KernelCtx &c, const void *src, double *dst, cudaStream_t st);
 // natural-order band from the factor records: 0 = l1, 1 = 1/M, 2 = l2, 3 = l3

@@ -156,6 +156,20 @@ __global__ void __launch_bounds__(kThreads) add_kernel(long long n, double *z,
         z[a] += y[a];
 }
 
+__global__ void __launch_bounds__(kThreads) to_f32_kernel(long long n, const double *__restrict__ x,
+                                                         float *y) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        y[a] = (float)x[a];
+}
+
+__global__ void __launch_bounds__(kThreads) from_f32_kernel(long long n, const float *__restrict__ x,
+                                                           double *y) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        y[a] = (double)x[a];
+}
+
 // Block sum of NV values per thread, written to red[blockIdx.x * NV + v], fixed order.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double *red) {
@@ -402,6 +416,16 @@ cudaError_t launch_resid_vec(const KernelCtx &c, const double *r, const double *
 
 cudaError_t launch_add(const KernelCtx &c, double *z, const double *y, cudaStream_t st) {
     add_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, z, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const KernelCtx &c, const double *x, float *y, cudaStream_t st) {
+    to_f32_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_f32(const KernelCtx &c, const float *x, double *y, cudaStream_t st) {
+    from_f32_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, x, y);
     return cudaGetLastError();
 }
 
