@@ -59,6 +59,7 @@ size_t carve(const ffp_grid *g, int prec, char *base, Ws *ws) {
     const size_t nlines = (size_t)g->ny * g->nz;
     w.rec = take(fb * nlines * (size_t)rec_len(S > 0 ? S : 1));
     w.l3 = take(fb * n);
+    w.l1 = take(fb * n);
     w.dinv = take(fb * n); w.lx = take(fb * n); w.ly = take(fb * n);
     w.r = (double *)take(8 * n); w.z = (double *)take(8 * n);
     w.p = (double *)take(8 * n); w.q = (double *)take(8 * n);

@@ -52,6 +52,8 @@ struct ApplyArgs {
     using R = typename Compute<F>::type;
     int nx, ny, nz;
     const F *rec;  // factor line records
+    const F *l3n;  // z-band of A in natural order (the twist-plane phase reads its second
+                   // coupling from here)
     const R *r;    // right-hand side
     R *z;          // output (holds y after the lower sweeps)
     R *scr;        // 2 planes of scratch (phase 2 intermediates)
@@ -71,8 +73,8 @@ constexpr int kSmemBudget = 220 * 1024;
 template <int S, typename F, int PH>
 struct Stage {
     using R = typename Compute<F>::type;
-    static constexpr int NF = (PH == 1) ? 5 : 4;  // eout, minv, l2, l3 (, second l3)
-    static constexpr int NM = (PH == 1) ? 4 : 3;  // twist-cell blocks: own, l2, l3 (, second l3)
+    static constexpr int NF = 5;  // alpha, gamma, minv, l2, l3
+    static constexpr int NM = 3;  // twist-cell blocks: own, l2, l3
     static constexpr int NV = (PH == 1) ? 3 : 2;
     static constexpr int kFld = 32 * S * (int)sizeof(F);
     static constexpr int kMid = 8 * (int)sizeof(F);
@@ -203,9 +205,11 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
                     v1 = A.z + row;                 // y, written by phase 0/1
                 }
             }
-            // record fields: [0] own eout, [1] own minv, [2] l2 row, [3] l3a, [4] l3b
-            const long src[5] = {own, own, l2r, l3a, l3b};
-            const int fld[5] = {REC_EOUT, REC_MINV, REC_L2, REC_L3, REC_L3};
+            // stage fields: [0..2] own alpha, gamma, minv, [3] l2 row, [4] l3a
+            // (the twist-plane phase's second coupling l3b is read from l3n)
+            (void)l3b;
+            const long src[5] = {own, own, own, l2r, l3a};
+            const int fld[5] = {REC_ALPHA, REC_GAMMA, REC_MINV, REC_L2, REC_L3};
             constexpr int CH = SG::kFld / 16;
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -218,11 +222,11 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
                             cp_async16(st + f * SG::kFld + (c0 + lane) * 16, gp + (c0 + lane) * 16);
                 }
             }
-            // twist-cell blocks: [0] own, [1] l2 row, [2] l3a, [3] l3b
+            // twist-cell blocks: [0] own, [1] l2 row, [2] l3a
             constexpr int MC = SG::kMid / 16;
             if (lane < NM * MC) {
                 const int j = lane / MC, c = lane % MC;
-                const long msrc = (j == 0) ? own : ((j == 1) ? l2r : ((j == 2) ? l3a : l3b));
+                const long msrc = (j == 0) ? own : ((j == 1) ? l2r : l3a);
                 if (msrc >= 0)
                     cp_async16(st + NF * SG::kFld + j * SG::kMid + c * 16,
                                reinterpret_cast<const unsigned char *>(A.rec + msrc * RL +
@@ -253,7 +257,8 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
         return;
     }
 
-    // stage accessors
+    // ------------------------------------------------------------------ compute
+    // stage accessors (fields, twist-cell blocks, vectors)
     auto F_ = [&](const unsigned char *st, int f, int s) -> R {
         return to_r(reinterpret_cast<const F *>(st + f * SG::kFld)[s * 32 + lane], R());
     };
@@ -263,36 +268,75 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
     auto V_ = [&](const unsigned char *st, int v, int s) -> R {
         return reinterpret_cast<const R *>(st + SG::kVecOff + v * SG::kVec)[s * 32 + lane];
     };
-    auto factor = [&](const unsigned char *st, LineFactor<S, R> &f) {
+    // vector slots of pads are never copied into: zero them once so that every
+    // slot can be computed without a validity test (their factors are 0 / 1)
+    if (VST) {
+        for (int q = 0; q < NST * NV; ++q) {
+            R *vb = reinterpret_cast<R *>(ring + (q / NV) * SG::kBytes + SG::kVecOff + (q % NV) * SG::kVec);
 #pragma unroll
-        for (int s = 0; s < S; ++s) { f.eout[s] = F_(st, 0, s); f.minv[s] = F_(st, 1, s); }
-        const R prev = __shfl_up_sync(0xffffffffu, f.eout[S - 1], 1, 16);
+            for (int s = 0; s < S; ++s)
+                if (s >= cnt) vb[s * 32 + lane] = R(0);
+        }
+    }
 #pragma unroll
-        for (int s = S - 1; s > 0; --s) f.ein[s] = f.eout[s - 1];
-        f.ein[0] = ((lane & 15) == 0) ? R(0) : prev;
-        f.minv_m = M_(st, 0, MID_MINV);
-        f.em1 = M_(st, 0, MID_EM1);
-        f.em = M_(st, 0, MID_EM);
-    };
+    for (int s = 0; s <= S; ++s) tcache[s * 32 + lane] = R(0);
+    __syncwarp();
 
-    // ------------------------------------------------------------------ compute
     R w[S], wm = R(0);
 #pragma unroll
     for (int s = 0; s < S; ++s) w[s] = R(0);
-    int g = 0;
-    // begin a step: wait until step g's stage is full
+    int slot = 0;
+    unsigned phase = 0;
+    // wait until the current stage is full
     auto begin = [&]() -> const unsigned char * {
-        const int slot = g % NST;
-        if (!aborted && !mbar_wait(full + slot, (g / NST) & 1)) {
+        if (!aborted && !mbar_wait(full + slot, phase)) {
             aborted = true;
             atomicOr(A.flags + FL_TIMEOUT, 1);
         }
         return ring + slot * SG::kBytes;
     };
-    // end a step: release step g's stage to the producer
+    // release the current stage to the producer and move to the next
     auto finish = [&]() {
         __syncwarp();
-        if (lane == 0) mbar_arrive(empty + g % NST);
+        if (lane == 0) mbar_arrive(empty + slot);
+        if (++slot == NST) { slot = 0; phase ^= 1u; }
+    };
+    // the line solve of a step from its stage
+    auto solve = [&](const unsigned char *st, const R (&b)[S], R bm, R (&x)[S], R &xm) {
+        R al[S], ga[S], mi[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) { al[s] = F_(st, 0, s); ga[s] = F_(st, 1, s); mi[s] = F_(st, 2, s); }
+        twisted_solve_pre<S, R>(al, ga, mi, M_(st, 0, MID_MINV), M_(st, 0, MID_EM1), M_(st, 0, MID_EM),
+                                cnt, lane, b, bm, x, xm);
+    };
+    // plane right-hand side v of cell slot s (s == S: twist cell) of a lower or
+    // twist step; NEAR: the coupled plane's row is read from global memory
+    const int nzv = nz;
+    auto rhs_v = [&](const unsigned char *st, int s, long row, const R *zrow, bool near,
+                     bool twist, int pl, int other) -> R {
+        const int a = (s == S) ? L.m : cell[s];
+        const R c3 = (s < S) ? F_(st, 4, s) : M_(st, 2, MID_L3);
+        R v;
+        if (PH == 0) {
+            v = VST ? V_(st, 0, s) : A.r[row + a];
+            if (other >= 0) {
+                const R yp = twist ? tcache[s * 32 + lane] : ((VST && !near) ? V_(st, 1, s) : zrow[a]);
+                v -= c3 * yp;
+            }
+        } else if (PH == 1) {
+            v = VST ? V_(st, 0, s) : A.r[row + a];
+            if (mz > 0) v -= c3 * (VST ? V_(st, 1, s) : A.z[row - nxy + a]);
+            if (mz < nzv - 1) {
+                const R c4 = to_r(A.l3n[row + a], R());   // coupling mz <-> mz+1
+                v -= c4 * (VST ? V_(st, 2, s) : A.z[row + nxy + a]);
+            }
+        } else {
+            R za;
+            if (twist && pl > 0) za = tcache[s * 32 + lane];
+            else za = (VST && (!near || pl == 0)) ? V_(st, 0, s) : zrow[a];
+            v = c3 * za;
+        }
+        return v;
     };
 
     for (int pl = 0; pl < npl; ++pl) {
@@ -303,44 +347,23 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
         const R *zo = (other >= 0) ? A.z + (long)other * nxy : A.z;
         R *scrp = A.scr + (long)h * nxy;
         // ------------------------------------------------------------ lower sweep
-        for (int t = 0; t < nl; ++t, ++g) {
+        // steps t < TN read the coupled plane's row directly (written fewer than NST steps ago)
+        constexpr int TN = (D + 1) / 2;
+        auto lower = [&](int t, bool near) {
             const unsigned char *st = begin();
             const int k = line_of(t);
             const long row = pbase + (long)k * nx;
-            LineFactor<S, R> f;
-            factor(st, f);
-            const bool far = 2 * t + 1 > D;
-            R b[S], bm = R(0);
+            const R *zrow = zo + (long)k * nx;
+            R b[S], bm;
 #pragma unroll
-            for (int s = 0; s <= S; ++s) {
-                const bool in = (s == S) || (s < cnt);
-                const int a = (s == S) ? L.m : cell[s];
-                R v = R(0);
-                if (in) {
-                    const R c3 = (s < S) ? F_(st, 3, s) : M_(st, 2, MID_L3);
-                    if (PH == 0) {
-                        v = VST ? V_(st, 0, s) : (R)A.r[row + a];
-                        if (other >= 0) {
-                            const R yp = (VST && far) ? V_(st, 1, s) : (R)zo[(long)k * nx + a];
-                            v -= c3 * yp;
-                        }
-                    } else if (PH == 1) {
-                        v = VST ? V_(st, 0, s) : (R)A.r[row + a];
-                        if (mz > 0) v -= c3 * (VST ? V_(st, 1, s) : (R)A.z[row - nxy + a]);
-                        if (mz < nz - 1) {
-                            const R c4 = (s < S) ? F_(st, 4, s) : M_(st, 3, MID_L3);
-                            v -= c4 * (VST ? V_(st, 2, s) : (R)A.z[row + nxy + a]);
-                        }
-                    } else {
-                        const R za = (VST && (far || pl == 0)) ? V_(st, 0, s) : (R)zo[(long)k * nx + a];
-                        v = c3 * za;
-                    }
-                    if (t > 0) v -= ((s < S) ? F_(st, 2, s) : M_(st, 1, MID_L2)) * ((s < S) ? w[s] : wm);
-                }
-                if (s < S) b[s] = v; else bm = v;
+            for (int s = 0; s < S; ++s) {
+                b[s] = rhs_v(st, s, row, zrow, near, false, pl, other);
+                if (t > 0) b[s] -= F_(st, 3, s) * w[s];
             }
+            bm = rhs_v(st, S, row, zrow, near, false, pl, other);
+            if (t > 0) bm -= M_(st, 1, MID_L2) * wm;
             R x[S], xm;
-            twisted_solve_fast<S, R>(f, cnt, lane, b, bm, x, xm);
+            solve(st, b, bm, x, xm);
             R *out = (PH == 2) ? scrp + (long)k * nx : A.z + row;
 #pragma unroll
             for (int s = 0; s < S; ++s) {
@@ -350,96 +373,74 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
             if (lane == 0) out[L.m] = xm;
             wm = xm;
             finish();
+        };
+        {
+            int t = 0;
+            for (; t < nl && t < TN; ++t) lower(t, true);
+            for (; t < nl; ++t) lower(t, false);
         }
         // ------------------------------------------------------------ twist line
         R u[S], um;
         {
             const unsigned char *st = begin();
             const long row = pbase + (long)my * nx;
-            LineFactor<S, R> f;
-            factor(st, f);
+            const R *zrow = zo + (long)my * nx;
             R *gw = gbuf + wid * nx;
 #pragma unroll
             for (int s = 0; s < S; ++s)
-                if (s < cnt) gw[cell[s]] = (nl > 0) ? F_(st, 2, s) * w[s] : R(0);
+                if (s < cnt) gw[cell[s]] = (nl > 0) ? F_(st, 3, s) * w[s] : R(0);
             if (lane == 0) gw[L.m] = (nl > 0) ? M_(st, 1, MID_L2) * wm : R(0);
-            R b[S], bm = R(0);
+            R b[S], bm;
 #pragma unroll
-            for (int s = 0; s <= S; ++s) {
-                const bool in = (s == S) || (s < cnt);
-                const int a = (s == S) ? L.m : cell[s];
-                R v = R(0);
-                if (in) {
-                    const R c3 = (s < S) ? F_(st, 3, s) : M_(st, 2, MID_L3);
-                    if (PH == 0) {
-                        v = VST ? V_(st, 0, s) : (R)A.r[row + a];
-                        if (other >= 0) v -= c3 * tcache[s * 32 + lane];
-                    } else if (PH == 1) {
-                        v = VST ? V_(st, 0, s) : (R)A.r[row + a];
-                        if (mz > 0) v -= c3 * (VST ? V_(st, 1, s) : (R)A.z[row - nxy + a]);
-                        if (mz < nz - 1) {
-                            const R c4 = (s < S) ? F_(st, 4, s) : M_(st, 3, MID_L3);
-                            v -= c4 * (VST ? V_(st, 2, s) : (R)A.z[row + nxy + a]);
-                        }
-                    } else {
-                        const R za = (pl == 0) ? (VST ? V_(st, 0, s) : (R)zo[(long)my * nx + a])
-                                               : tcache[s * 32 + lane];
-                        v = c3 * za;
-                    }
-                }
-                if (s < S) b[s] = v; else bm = v;
-            }
+            for (int s = 0; s < S; ++s) b[s] = rhs_v(st, s, row, zrow, false, true, pl, other);
+            bm = rhs_v(st, S, row, zrow, false, true, pl, other);
             named_barrier(1, 64);
 #pragma unroll
             for (int s = 0; s < S; ++s)
                 if (s < cnt) b[s] = b[s] - gbuf[cell[s]] - gbuf[nx + cell[s]];
             bm = bm - gbuf[L.m] - gbuf[nx + L.m];
-            twisted_solve_fast<S, R>(f, cnt, lane, b, bm, u, um);
+            solve(st, b, bm, u, um);
             // final value of the twist line: u (phases 0, 1) or y - u (phase 2)
 #pragma unroll
             for (int s = 0; s <= S; ++s) {
-                const bool in = (s == S) || (s < cnt);
-                if (!in) continue;
                 const int a = (s == S) ? L.m : cell[s];
                 const R uu = (s < S) ? u[s] : um;
                 R fin = uu;
-                if (PH == 2) fin = (VST ? V_(st, 1, s) : (R)A.z[row + a]) - uu;
+                if (PH == 2) fin = (VST ? V_(st, 1, s) : A.z[row + a]) - uu;
                 tcache[s * 32 + lane] = fin;
-                if (wid == 0 && (s < S || lane == 0)) A.z[row + a] = fin;
+                if (wid == 0 && ((s < S && s < cnt) || (s == S && lane == 0))) A.z[row + a] = fin;
             }
             finish();
-            ++g;
         }
         // ------------------------------------------------------------ upper sweep
-        for (int t = nl - 1; t >= 0; --t, ++g) {
+        // the first D/2 steps read the lower-sweep row directly (written < NST steps ago)
+        auto upper = [&](int t, bool near) {
             const unsigned char *st = begin();
             const int k = line_of(t);
             const long row = pbase + (long)k * nx;
-            LineFactor<S, R> f;
-            factor(st, f);
-            const bool far = 2 * (nl - t) > D;
             R b[S], bm;
 #pragma unroll
-            for (int s = 0; s < S; ++s) b[s] = F_(st, 2, s) * u[s];
+            for (int s = 0; s < S; ++s) b[s] = F_(st, 3, s) * u[s];
             bm = M_(st, 1, MID_L2) * um;
             R x[S], xm;
-            twisted_solve_fast<S, R>(f, cnt, lane, b, bm, x, xm);
+            solve(st, b, bm, x, xm);
             const R *wrow = (PH == 2) ? scrp + (long)k * nx : A.z + row;
 #pragma unroll
             for (int s = 0; s <= S; ++s) {
-                const bool in = (s == S) || (s < cnt);
                 const int a = (s == S) ? L.m : cell[s];
-                R uu = R(0);
-                if (in) {
-                    const R wv = (VST && far) ? V_(st, 0, s) : (R)wrow[a];
-                    uu = wv - ((s < S) ? x[s] : xm);
-                    R fin = uu;
-                    if (PH == 2) fin = (VST ? V_(st, 1, s) : (R)A.z[row + a]) - uu;
-                    if (s < S || lane == 0) A.z[row + a] = fin;
-                }
+                const R wv = (VST && !near) ? V_(st, 0, s) : wrow[a];
+                const R uu = wv - ((s < S) ? x[s] : xm);
+                R fin = uu;
+                if (PH == 2) fin = (VST ? V_(st, 1, s) : A.z[row + a]) - uu;
+                if ((s < S && s < cnt) || (s == S && lane == 0)) A.z[row + a] = fin;
                 if (s < S) u[s] = uu; else um = uu;
             }
             finish();
+        };
+        {
+            int t = nl - 1;
+            for (; t >= 0 && 2 * (nl - t) <= D; --t) upper(t, true);
+            for (; t >= 0; --t) upper(t, false);
         }
     }
 }
@@ -461,6 +462,7 @@ cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cuda
     ApplyArgs<F> a;
     a.nx = c.nx; a.ny = c.ny; a.nz = c.nz;
     a.rec = (const F *)c.ws.rec;
+    a.l3n = (const F *)c.ws.l3;
     a.scr = reinterpret_cast<R *>(c.ws.ascr);
     a.flags = c.ws.flags;
     cudaError_t e = cudaSuccess;

@@ -244,6 +244,65 @@ __device__ __forceinline__ void twisted_solve_fast(const LineFactor<S, R> &f, in
     xm = ym;
 }
 
+// The same solve from precomputed multipliers (factor line records): al =
+// forward multiplier, ga = backward multiplier (both 1 on pads), mi = 1/M
+// (0 on pads), and the twist cell.  Pads need no selects except in the
+// backward own terms, which must vanish on pads.
+template <int S, typename R>
+__device__ __forceinline__ void twisted_solve_pre(const R (&al)[S], const R (&ga)[S],
+                                                  const R (&mi)[S], R minv_m, R em1, R em,
+                                                  int cnt, int lane, const R (&b)[S], R bm,
+                                                  R (&x)[S], R &xm) {
+    const int j = lane & 15;
+    const unsigned FULL = 0xffffffffu;
+    R pa[S], pb[S];
+    R A = R(1), B = R(0);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        B = fma(al[s], B, mi[s] * b[s]);
+        A = A * al[s];
+        pa[s] = A;
+        pb[s] = B;
+    }
+    R Xa[S], Xb[S], Gs[S];
+    {
+        R xa = R(0), xb = R(0), gs = R(1);
+#pragma unroll
+        for (int s = S - 1; s >= 0; --s) {
+            const bool v = s < cnt;
+            xa = fma(ga[s], xa, v ? pa[s] : R(0));
+            xb = fma(ga[s], xb, v ? pb[s] : R(0));
+            gs = ga[s] * gs;
+            Xa[s] = xa; Xb[s] = xb; Gs[s] = gs;
+        }
+    }
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const R Au = __shfl_up_sync(FULL, A, d, 16);
+        const R Bu = __shfl_up_sync(FULL, B, d, 16);
+        if (j >= d) { B = fma(A, Bu, B); A = A * Au; }
+    }
+    R c = __shfl_up_sync(FULL, B, 1, 16);
+    if (j == 0) c = R(0);
+    const R ytop = __shfl_sync(FULL, B, 15);
+    const R ybot = __shfl_sync(FULL, B, 31);
+    R G = Gs[0];
+    R Bb = fma(Xa[0], c, Xb[0]);
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const R Gd = __shfl_down_sync(FULL, G, d, 16);
+        const R Bd = __shfl_down_sync(FULL, Bb, d, 16);
+        if (j + d < 16) { Bb = fma(G, Bd, Bb); G = G * Gd; }
+    }
+    const R ym = minv_m * (bm - em1 * ytop - em * ybot);
+    const R Gn = __shfl_down_sync(FULL, G, 1, 16);
+    const R Bn = __shfl_down_sync(FULL, Bb, 1, 16);
+    const R cin = (j == 15) ? ym : fma(Gn, ym, Bn);
+#pragma unroll
+    for (int s = 0; s < S; ++s) x[s] = fma(Gs[s], cin, fma(Xa[s], c, Xb[s]));
+    xm = ym;
+}
+
 // ---------------------------------------------------------------- level-1 pivots
 // Twisted pivots of the tridiagonal T (recurrence for M_i, Sec. II-A):
 // M[c] = D[c] - ein[c]^2 / M[c-1] along each chain, and at the twist cell
@@ -330,16 +389,17 @@ __device__ __forceinline__ void twisted_pivots(int cnt, int lane, const double (
 
 // ---------------------------------------------------------------- factor line records
 // The apply reads the stored factors line by line in the warp's own order, so
-// they are stored as one record per line (i, k), record index i*ny + k:
-//   field 0 eout[S][32]  coupling of the cell towards the twist cell
-//                        (top chain: l1[a]; bottom chain: l1[a-1])
-//   field 1 minv[S][32]  1 / M_a
-//   field 2 l2[S][32]    y-band of P_i: coupling of cell a of line k with line k+1
-//   field 3 l3[S][32]    z-band of A: coupling of cell a of plane i with plane i+1
-//   mid[8]               the twist cell: 1/M_m, T[m-1,m], T[m,m+1], l2, l3, 0, 0, 0
-// [s][32] is slot s of lanes 0..31; pads hold 0.  A record is a multiple of 16
-// bytes, so a warp pulls it with 16-byte asynchronous copies.
-enum { REC_EOUT = 0, REC_MINV = 1, REC_L2 = 2, REC_L3 = 3, REC_NFIELD = 4 };
+// they are stored as one record per line (i, k), record index i*ny + k, with
+// the multipliers of the twisted line solve precomputed:
+//   field 0 alpha[S][32]  -minv_a * (coupling to the chain predecessor)  (pads 1)
+//   field 1 gamma[S][32]  -minv_a * (coupling towards the twist cell)    (pads 1)
+//   field 2 minv[S][32]   1 / M_a                                        (pads 0)
+//   field 3 l2[S][32]     y-band of P_i: coupling of cell a of line k with line k+1 (pads 0)
+//   field 4 l3[S][32]     z-band of A: coupling of cell a of plane i with plane i+1 (pads 0)
+//   mid[8]                the twist cell: 1/M_m, T[m-1,m], T[m,m+1], l2, l3, 0, 0, 0
+// [s][32] is slot s of lanes 0..31.  A record is a multiple of 16 bytes, so a
+// warp pulls it with 16-byte asynchronous copies.
+enum { REC_ALPHA = 0, REC_GAMMA = 1, REC_MINV = 2, REC_L2 = 3, REC_L3 = 4, REC_NFIELD = 5 };
 enum { MID_MINV = 0, MID_EM1 = 1, MID_EM = 2, MID_L2 = 3, MID_L3 = 4, REC_NMID = 8 };
 
 __host__ __device__ __forceinline__ long rec_len(int S) { return (long)REC_NFIELD * 32 * S + REC_NMID; }
@@ -438,9 +498,10 @@ inline int slots_for(int nx) {
 struct Ws {
     // operator bands (FP64)
     double *d, *cx, *cy, *cz;
-    // factors in storage precision: one record per line (see rec_len), and l3 =
-    // z-band of A in natural order (for the ILU(0) sweeps)
-    void *rec, *l3;
+    // factors in storage precision: one record per line (see rec_len), l3 =
+    // z-band of A in natural order (for the ILU(0) sweeps), l1 = x-band of T in
+    // natural order (kept for ffp_export)
+    void *rec, *l3, *l1;
     // combination preconditioner: ILU(0) 1/D and the x, y bands of A in storage precision
     void *dinv, *lx, *ly;
     // combination temporaries

@@ -84,26 +84,17 @@ __global__ void l3_records_kernel(Geo g, int S, const double *__restrict__ cz, F
     }
 }
 
-// natural-order l1 (x-band of T), 1/M, l2 or l3 from the records (what: 0..3)
+// natural-order 1/M, l2 or l3 from the records (what: 1..3)
 template <typename F>
 __global__ void export_rec_kernel(Geo g, int S, const F *__restrict__ rec, int what, double *o) {
     using R = typename Compute<F>::type;
-    const int m = (g.nx - 1) / 2;
+    const int f = (what == 1) ? REC_MINV : ((what == 2) ? REC_L2 : REC_L3);
+    const int mf = (what == 1) ? MID_MINV : ((what == 2) ? MID_L2 : MID_L3);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < g.n;
          a += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(a % g.nx);
         const F *rb = rec + (a / g.nx) * rec_len(S);
-        double v = 0.0;
-        if (what == 1) v = (double)to_r(rb[rec_cell(g.nx, S, REC_MINV, MID_MINV, x)], R());
-        else if (what == 2) v = (double)to_r(rb[rec_cell(g.nx, S, REC_L2, MID_L2, x)], R());
-        else if (what == 3) v = (double)to_r(rb[rec_cell(g.nx, S, REC_L3, MID_L3, x)], R());
-        else {
-            // T[x, x+1]: eout of x in the top chain, of x+1 in the bottom chain
-            if (x < m) v = (double)to_r(rb[rec_cell(g.nx, S, REC_EOUT, 0, x)], R());
-            else if (x == m) v = (x + 1 < g.nx) ? (double)to_r(rb[(long)REC_NFIELD * 32 * S + MID_EM], R()) : 0.0;
-            else v = (x + 1 < g.nx) ? (double)to_r(rb[rec_cell(g.nx, S, REC_EOUT, 0, x + 1)], R()) : 0.0;
-        }
-        o[a] = v;
+        o[a] = (double)to_r(rb[rec_cell(g.nx, S, f, mf, x)], R());
     }
 }
 
@@ -374,6 +365,7 @@ cudaError_t launch_convert_bands(const KernelCtx &c, cudaStream_t st) {
 }
 
 cudaError_t launch_export_rec(const KernelCtx &c, int what, double *dst, cudaStream_t st) {
+    if (what == 0) return launch_export(c, c.ws.l1, dst, st);
     switch (c.prec) {
         case FFP_FP64:
             export_rec_kernel<double><<<grid_for(c.n), kThreads, 0, st>>>(geo(c), c.slots, (const double *)c.ws.rec, what, dst);

@@ -31,6 +31,7 @@ struct SetupArgs {
     const double *d, *cx, *cy, *cz;
     const double *t;  // filter, NULL = rowsum
     void *rec;        // factor line records (rec_len(S) entries per line)
+    void *l1n;        // natural-order x-band of T (for export)
     Ws ws;
 };
 
@@ -164,26 +165,32 @@ __device__ __forceinline__ void factor_line(const LineMap &L, int lane, int cnt,
 }
 
 // Store line k of the plane: FP64 natural-order copies for the setup's own
-// plane solves (l1d, mid) and the line record line0 + k (eout, 1/M, twist cell).
+// plane solves (l1d, mid), the natural-order l1 (for export) and the line
+// record line0 + k: the line solve's multipliers -1/M * coupling (forward and
+// backward), 1/M and the twist cell.
 template <int S>
 __device__ __forceinline__ void store_line(const LineMap &L, int lane, int cnt, int nx, int k,
                                            const LineState<S> &st, double *l1d, double *mid,
-                                           void *rec, long line0, int prec) {
+                                           void *rec, void *l1n, long line0, int prec) {
     const long o = (long)k * nx;
     const long rb = (line0 + k) * rec_len(S);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        if (s < cnt) {
+        const bool v = s < cnt;
+        if (v) {
             const int a = slot_cell<S>(L, lane, s);
             l1d[o + a] = st.To[s];
             mid[o + a] = st.f.minv[s];
+            put_factor(l1n, (line0 + k) * nx + a, st.To[s], prec);
         }
-        put_factor(rec, rb + (long)REC_EOUT * 32 * S + s * 32 + lane, s < cnt ? st.f.eout[s] : 0.0, prec);
-        put_factor(rec, rb + (long)REC_MINV * 32 * S + s * 32 + lane, s < cnt ? st.f.minv[s] : 0.0, prec);
+        put_factor(rec, rb + (long)REC_ALPHA * 32 * S + s * 32 + lane, v ? -st.f.minv[s] * st.f.ein[s] : 1.0, prec);
+        put_factor(rec, rb + (long)REC_GAMMA * 32 * S + s * 32 + lane, v ? -st.f.minv[s] * st.f.eout[s] : 1.0, prec);
+        put_factor(rec, rb + (long)REC_MINV * 32 * S + s * 32 + lane, v ? st.f.minv[s] : 0.0, prec);
     }
     if (lane == 0) {
         l1d[o + L.m] = st.Tom;
         mid[o + L.m] = st.f.minv_m;
+        put_factor(l1n, (line0 + k) * nx + L.m, st.Tom, prec);
         const long mb = rb + (long)REC_NFIELD * 32 * S;
         put_factor(rec, mb + MID_MINV, st.f.minv_m, prec);
         put_factor(rec, mb + MID_EM1, st.f.em1, prec);
@@ -197,8 +204,9 @@ __device__ __forceinline__ void store_line(const LineMap &L, int lane, int cnt, 
 template <int S>
 __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
                              const double *Px, const double *Py, const double *tp, double *l1d,
-                             double *mid, void *rec, long line0, int prec, double *lbuf,
-                             double *meet, int wid, int lane, int cnt, int *flags) {
+                             double *mid, void *rec, void *l1n, long line0, int prec,
+                             double *lbuf, double *meet, int wid, int lane, int cnt,
+                             int *flags) {
     const int my = (ny - 1) / 2;
     const int nl = (wid == 0) ? my : ny - 1 - my;
     double *SB = lbuf + wid * 3 * nx, *SP = SB + nx, *SO = SP + nx;
@@ -229,7 +237,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
             Tom -= com;
         }
         factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags);
-        store_line<S>(L, lane, cnt, nx, k, st, l1d, mid, rec, line0, prec);
+        store_line<S>(L, lane, cnt, nx, k, st, l1d, mid, rec, l1n, line0, prec);
     }
     // twist line: Schur terms from both halves
     {
@@ -266,7 +274,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
         Tdm = Pd[o + L.m] - meet[L.m] - meet[2 * nx + L.m];
         Tom = Px[o + L.m] - meet[nx + L.m] - meet[3 * nx + L.m];
         factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags);
-        if (wid == 0) store_line<S>(L, lane, cnt, nx, my, st, l1d, mid, rec, line0, prec);
+        if (wid == 0) store_line<S>(L, lane, cnt, nx, my, st, l1d, mid, rec, l1n, line0, prec);
     }
 }
 
@@ -302,7 +310,8 @@ __global__ void __launch_bounds__(256) setup_kernel(SetupArgs A, int phase) {
                            Py[e], A.prec);
             if (wid < 2)
                 level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + i * nxy : nullptr, l1d, mid,
-                                A.rec, (long)i * ny, A.prec, lbuf, meet, wid, lane, cnt, flags);
+                                A.rec, A.l1n, (long)i * ny, A.prec, lbuf, meet, wid, lane, cnt,
+                                flags);
             const int dst = (t == nl3 - 1) ? mz : ((h == 0) ? i + 1 : i - 1);
             const int ic = (i < dst) ? i : dst;
             const double *C = A.cz + ic * nxy;
@@ -362,8 +371,8 @@ __global__ void __launch_bounds__(256) setup_kernel(SetupArgs A, int phase) {
         __syncthreads();
         if (wid < 2)
             level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + g0 : nullptr, A.ws.sF[0][0],
-                            A.ws.sF[0][1], A.rec, (long)mz * ny, A.prec, lbuf, meet, wid, lane,
-                            cnt, flags);
+                            A.ws.sF[0][1], A.rec, A.l1n, (long)mz * ny, A.prec, lbuf, meet, wid,
+                            lane, cnt, flags);
     }
 }
 
@@ -374,6 +383,7 @@ cudaError_t setup_for_slots(const KernelCtx &c, const double *t, cudaStream_t st
     a.d = c.ws.d; a.cx = c.ws.cx; a.cy = c.ws.cy; a.cz = c.ws.cz;
     a.t = t;
     a.rec = c.ws.rec;
+    a.l1n = c.ws.l1;
     a.ws = c.ws;
     const size_t smem = sizeof(double) * 14 * (size_t)a.nx;
     cudaError_t e = cudaFuncSetAttribute(setup_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
