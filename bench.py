@@ -8,7 +8,7 @@ HBM.  `e2e` repeats the step through the public API from pinned host buffers
 (kappa and b copied in, x copied out inside the timed region).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload grf350|layered128|blocks32] [--precision fp32|fp64|bf16]
+                  [--workload grf350|layered128|blocks32|batched] [--precision fp32|fp64|bf16]
                   [--precond combo|ntd]
 
 --impl reference times the CPU oracle (plain C, FP64, one core) on a bounded
@@ -28,6 +28,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -35,10 +37,11 @@ METRIC = "PCG s to rel-res 1e-8 at 350^3 (learned+FP32 vs plain FP64); apply GB/
 RTOL = 1e-8
 MAXIT = 1000
 
-# algorithmic bytes per unknown of one B_NTD apply: 2 sweeps x 4 factor arrays
-# (l1, 1/M, l2, l3) in the storage precision + 4 FP64 vector passes (read r,
-# write y, read y, write z)
-NTD_BYTES = {"fp64": 2 * 4 * 8 + 4 * 8, "fp32": 2 * 4 * 4 + 4 * 8, "bf16": 2 * 4 * 2 + 4 * 8}
+# algorithmic bytes per unknown of one B_NTD apply (the three sweep launches):
+# 2 sweeps x 4 factor arrays (l1, 1/M, l2, l3) in the storage precision + 4
+# vector passes (read r, write y, read y, write z) in the apply's arithmetic
+# type (FP64 for FP64 factors, FP32 otherwise)
+NTD_BYTES = {"fp64": 2 * 4 * 8 + 4 * 8, "fp32": 2 * 4 * 4 + 4 * 4, "bf16": 2 * 4 * 2 + 4 * 4}
 
 
 def make_workload(name, seed=0):
@@ -61,6 +64,9 @@ def describe(name):
                   "[-1,1] (contrast 10^6); b ~ N(0,1)",
         "layered128": "128^3, 16 z-layers kappa 1/1e6 with eight 16^3 inclusions 1e-3; b = h^3",
         "blocks32": "32^3, kappa 10^e on 4x4x4 blocks, e in [-3,3]; b ~ N(0,1)",
+        "batched": "64 instances, nx,ny,nz ~ U[48,160] each (uneven), kappa 10^e on 8x8x8 blocks, "
+                   "e in [-3,3], Dirichlet z-faces, Neumann x/y; 4 right-hand sides N(0,1) each "
+                   "(256 solves per step)",
     }.get(name, name)
 
 
@@ -125,6 +131,26 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(workload, seed, rank):
+    """Seed of rank `rank`'s replica: every rank solves its own independent
+    problem (the solve does not shard), so the ranks' inputs must differ.  A
+    batched replica spans seeds seed' .. seed' + 63 (one per instance), hence
+    the stride of 1000."""
+    return seed + (1000 * rank if workload == "batched" else rank)
+
+
+def max_over_ranks(values, device, world_size):
+    """Element-wise maximum over ranks of a list of floats (the job's time is
+    its slowest rank's)."""
+    if world_size <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -135,7 +161,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = make_workload(args.workload, seed=args.seed + rank)
+    w = make_workload(args.workload, seed=replica_seed(args.workload, args.seed, rank))
     grid, bc = w["grid"], w["bc"]
     n = int(w["kappa"].size)
     kappa_h = torch.from_numpy(w["kappa"]).pin_memory()
@@ -194,10 +220,7 @@ def run_ours(args):
         e2.append(t0.elapsed_time(t1))
     barrier()
     e2e_ms = sum(e2) / len(e2)
-    if ws > 1:
-        t = torch.tensor([ms, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev, ws)
     st = stats[-1]
     ok = all(s["status"] == 0 and s["rel_res_true"] < RTOL for s in stats)
     peak, peak_kind = load_peaks()
@@ -259,6 +282,175 @@ def run_ours(args):
         print(json.dumps(line))
 
 
+def run_batched(args):
+    """The batched workload: every step sets up all 64 instances and solves
+    all 256 (instance, right-hand side) pairs to rtol in one batch, launch
+    configuration from the autotuner (tuned once, in the first warm-up step)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1909_09771_gb300 import ffp
+    from paper_1909_09771_gb300 import inputs as I
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nrhs = 4
+    insts = I.workload_batched(seed=replica_seed("batched", args.seed, rank), nrhs=nrhs)
+    grids = [w["grid"] for w in insts]
+    bcs = [w["bc"] for w in insts]
+    ns = [int(np.prod(g)) for g in grids]
+    kap_h = [torch.from_numpy(w["kappa"]).pin_memory() for w in insts]
+    b_h = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory() for w in insts for b in w["b"]]
+    x_h = [torch.empty(ns[p // nrhs], dtype=torch.float64).pin_memory() for p in range(len(b_h))]
+    kap = [k.to(dev) for k in kap_h]
+    bs = [b.to(dev) for b in b_h]
+    xs = [torch.zeros_like(b) for b in bs]
+    stream = torch.cuda.current_stream(dev)
+    wsb = ffp.batch_workspace_bytes(grids, nrhs, args.precision)
+    work = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    tuned = {}
+
+    def step(kaps, rhs, xout):
+        bat = ffp.Batch(grids, kaps, bcs, nrhs=nrhs, precision=args.precision,
+                        precond=args.precond, workspace=work)
+        if not tuned:
+            tuned.update(bat.tune())
+        else:
+            bat.set_config(tuned["ilu_warps"], tuned["branches"])
+        for x in xout:
+            x.zero_()
+        _, stats = bat.solve(rhs, xs=xout, rtol=RTOL, maxit=MAXIT, check=False)
+        info = bat.info()
+        bat.close()
+        return stats, info
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        stats, info = step(kap, bs, xs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs = []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            runs.append(step(kap, bs, xs))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    e2 = []
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        kd = [k.to(dev, non_blocking=True) for k in kap_h]
+        bd = [b.to(dev, non_blocking=True) for b in b_h]
+        step(kd, bd, xs)
+        for xh, xd in zip(x_h, xs):
+            xh.copy_(xd, non_blocking=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        e2.append(t0.elapsed_time(t1))
+    barrier()
+    e2e_ms = sum(e2) / len(e2)
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev, ws)
+    stats, info = runs[-1]
+    ok = all(s["status"] == 0 and s["rel_res_true"] < RTOL for st, _ in runs for s in st)
+    iters = [s["iters"] for s in stats]
+    peak, peak_kind = load_peaks()
+    pair_unknowns = sum(ns[p // nrhs] for p in range(len(bs)))
+    algo_bytes = NTD_BYTES[args.precision] * pair_unknowns
+    ntd_ms = tuned.get("ntd_ms", 0.0)
+    achieved = algo_bytes / (ntd_ms * 1e-3) / 1e9 if ntd_ms > 0 else None
+    line = {
+        "metric": METRIC,
+        "value": ms / 1e3 / ws,
+        "unit": "s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64+f32" if args.precision != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "batched: " + describe("batched"),
+            "precond": {"combo": "B_c = NTD + ILU(0) (Sec. III Eq. (com))",
+                        "ntd": "B_NTD (Sec. II)"}[args.precond],
+            "factors": args.precision,
+            "filter": "rowsum",
+            "rtol": RTOL,
+            "unknowns": sum(ns),
+            "pairs": len(bs),
+            "pair_unknowns_per_s": pair_unknowns / (ms / 1e3) * ws,
+            "iters_mean": float(np.mean(iters)),
+            "iters_max": int(max(iters)),
+            "converged": ok,
+            "tuned": tuned,
+            "groups": info["groups"],
+            "replicas": ws,
+            "l2": "inputs larger than L2 (the batch's vectors total several GB)",
+        },
+        "roofline": {
+            "kernel": "apply_kernel (B_NTD sweeps of all 256 pairs, 3 launches per slot-count group)",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "peak_kind": peak_kind,
+            "traffic": None,
+            "algorithmic_bytes_per_apply": algo_bytes,
+            "ms_per_apply": ntd_ms,
+        },
+        "e2e": {"value": e2e_ms / 1e3 / ws, "unit": "s",
+                "h2d_bytes_per_step": 8 * (sum(ns) + pair_unknowns),
+                "d2h_bytes_per_step": 8 * pair_unknowns},
+        "gpu_launches": int(sum(st[0]["launches"] + inf["setup_launches"] for st, inf in runs)),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batched(insts, iters, nrhs)
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def cpu_baseline_batched(insts, iters, nrhs):
+    """The oracle on a bounded sample of the batch: instance 0's assembly +
+    setup + ILU(0) pivots and one B_c flexible-CG iteration, measured, then
+    scaled by unknowns to every instance's setup and every pair's iterations."""
+    from oracle import oracle as O
+    w = insts[0]
+    g = w["grid"]
+    n0 = int(np.prod(g))
+    t0 = time.perf_counter()
+    bands = O.assemble(g, w["kappa"], w["bc"])
+    f = O.setup(g, bands)
+    D = O.ilu0_setup(g, bands)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.pcg(g, bands, f, w["b"][0], rtol=1e-300, maxit=1, flexible=True, ilu=D)
+    t_iter = time.perf_counter() - t0
+    ns = [int(np.prod(x["grid"])) for x in insts]
+    total = t_setup / n0 * sum(ns) + t_iter / n0 * sum(iters[p] * ns[p // nrhs] for p in range(len(iters)))
+    return {"value": total, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"instance 0 ({g[0]}x{g[1]}x{g[2]}): setup {t_setup:.2f} s and one B_c "
+                      f"flexible-CG iteration {t_iter:.2f} s measured, scaled by unknowns to all "
+                      f"{len(insts)} setups and {len(iters)} solves ({sum(iters)} iterations)"}
+
+
 def cpu_baseline(w, iters, sample_iters):
     """The oracle as it stands, one host core: assembly + setup + ILU(0) pivots
     measured in full, plus `sample_iters` flexible-CG iterations with B_c; the
@@ -286,11 +478,19 @@ def run_reference(args):
         return
     from oracle import oracle as O
     O.build()
-    w = make_workload(args.workload, seed=args.seed)
     iters = REFERENCE_ITERS.get(args.workload)
+    if args.workload == "batched":
+        from paper_1909_09771_gb300 import inputs as I
+        insts = I.workload_batched(seed=args.seed)
+        per_pair = [iters] * (4 * len(insts))
+    else:
+        w = make_workload(args.workload, seed=args.seed)
     times = []
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(w, iters if iters else 1, 1)
+        if args.workload == "batched":
+            cb = cpu_baseline_batched(insts, per_pair, 4)
+        else:
+            cb = cpu_baseline(w, iters if iters else 1, 1)
         if k >= args.warmup:
             times.append(cb["value"])
     v = sum(times) / len(times)
@@ -308,8 +508,9 @@ def run_reference(args):
 
 # Iterations B_c flexible CG takes to rtol 1e-8 on each workload (seed 0), as
 # counted by the library's FP64 solve, whose arithmetic matches the oracle's
-# (the parity tests hold the two iteration counts within one).
-REFERENCE_ITERS = {"grf350": 159, "blocks32": 22}
+# (the parity tests hold the two iteration counts within one); for the batched
+# workload the mean over its 256 pairs (library, FP32 factors).
+REFERENCE_ITERS = {"grf350": 159, "blocks32": 22, "batched": 98}
 
 
 def main():
@@ -327,6 +528,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

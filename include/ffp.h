@@ -80,7 +80,8 @@ typedef struct {
     double rel_res_true;  /* ||b - A x|| / ||b|| recomputed at exit */
     double solve_s;       /* wall time of the solve (host clock, after a stream sync) */
     double precond_ms;    /* device time of all preconditioner applies (CUDA events on `stream`) */
-    double ntd_ms;        /* device time of their B_NTD sweeps (the apply kernels) */
+    double ntd_ms;        /* device time of their B_NTD sweeps: the three apply kernel launches
+                             of each apply, precision conversions excluded */
     int napply;           /* number of preconditioner applies */
     long long launches;   /* kernels this call launched */
 } ffp_stats;
@@ -191,6 +192,83 @@ int ffp_apply_noalloc(ffp_handle *h, const double *r, double *z, void *stream);
 
 /* Free the host handle (no device memory is freed). */
 void ffp_destroy(ffp_handle *h);
+
+/* ------------------------------------------------------------------------
+ * Batched solves: many independent problems at once.  The paper solves one
+ * problem at a time; batching is this library's way of filling one GPU with
+ * the independent level-3 chains of many problems.  A batch holds `count`
+ * instances, each with its own grid (uneven sizes allowed), kappa, boundary
+ * conditions and preconditioner (Sec. II / III, as built by ffp_setup), and
+ * `nrhs` right-hand sides per instance; a "pair" is one (instance, right-hand
+ * side), numbered i * nrhs + j.  Every pair's result is the one its
+ * standalone ffp_setup + ffp_pcg_solve would give with the same arguments
+ * (same iterations; the same solution up to rounding of an identical
+ * sequence of operations).
+ * ------------------------------------------------------------------------ */
+typedef struct ffp_batch ffp_batch;
+
+#define FFP_BATCH_MAX_PAIRS 65535  /* count * nrhs (the pair is a grid's y index) */
+
+/* Launch configuration chosen by ffp_batch_tune.  It never changes a result. */
+typedef struct {
+    int ilu_warps;   /* lines per CTA of the ILU(0) sweeps (1..8) */
+    int branches;    /* 1: the slot-count groups run as parallel graph branches; 0: in sequence */
+    double ms;       /* mean time (ms) of one preconditioner application to every pair
+                        under this configuration, as timed by ffp_batch_tune */
+    double ntd_ms;   /* mean time (ms) of the B_NTD sweeps alone (3 launches per group) */
+    int from_cache;  /* 1 if read from the tuning cache */
+} ffp_batch_config;
+
+/* Bytes of the one device workspace of a batch (0 for invalid arguments).
+ *   grids  host array [count]; precision as for ffp_workspace_bytes */
+size_t ffp_batch_workspace_bytes(int count, const ffp_grid *grids, int nrhs, int precision);
+
+/* Assemble and set up every instance, on `stream`, and return a host handle.
+ *   grids, bcs  host arrays [count]
+ *   kappa       host array [count] of device FP64 [N_i] pointers
+ *   t           NULL (rowsum filters), or a host array [count] of device FP64
+ *               [N_i] filter pointers, NULL entries meaning rowsum
+ *   precision, precond  as for ffp_setup, for every instance
+ *   workspace   device memory, 256-byte aligned, >= ffp_batch_workspace_bytes
+ * Calls no device allocator; it creates streams and events and pins a little
+ * host memory.  Returns FFP_ERR_ARG, FFP_ERR_BREAKDOWN (some instance's setup
+ * broke down) or FFP_ERR_CUDA, and then no handle. */
+int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa,
+                    const ffp_bc *bcs, const double *const *t, int nrhs, int precision,
+                    int precond, void *workspace, size_t ws_bytes, void *stream, ffp_batch **out);
+
+/* Choose the launch configuration by timing the batched preconditioner on
+ * this batch (it overwrites the pairs' internal vectors, none of the caller's).
+ * cache_path: NULL, or a text file of "<key> <ilu_warps> <branches> <ms> <ntd_ms>"
+ * lines; a line whose key (GPU, precision, preconditioner, grids, nrhs)
+ * matches is used without timing (ms and ntd_ms are then the cached ones),
+ * else the choice is appended.  out may be NULL.  A batch that is never tuned
+ * uses ilu_warps 4, branches 1. */
+int ffp_batch_tune(ffp_batch *B, const char *cache_path, ffp_batch_config *out, void *stream);
+int ffp_batch_get_config(const ffp_batch *B, ffp_batch_config *cfg);
+int ffp_batch_set_config(ffp_batch *B, const ffp_batch_config *cfg);
+
+/* Groups (pairs of one slot count), pairs, kernels one batched CG iteration
+ * launches, and kernels ffp_batch_setup launched.  Any output pointer may be NULL. */
+int ffp_batch_info(const ffp_batch *B, int *ngroups, int *npairs, long long *launches_per_iter,
+                   long long *setup_launches);
+
+/* Solve every pair: PCG / flexible CG exactly as ffp_pcg_solve, all pairs
+ * advancing together, each stopping on its own test.  One iteration of all
+ * pairs is one CUDA graph launch, captured on the first solve and kept
+ * until the configuration changes.
+ *   b, x   host arrays [count * nrhs] of device FP64 [N_i] pointers (x: in x0,
+ *          out the solution), indexed by pair
+ *   stats  NULL or host array [count * nrhs]
+ * The solve is synchronous: it waits for prior work on `stream`, and returns
+ * once every pair is done.  It returns FFP_OK if every pair converged, else
+ * the first failing pair's status (per-pair status in stats).  Calls on one
+ * batch must not overlap. */
+int ffp_batch_solve(ffp_batch *B, const double *const *b, double *const *x, double rtol, int maxit,
+                    ffp_stats *stats, void *stream);
+
+/* Free the batch's host state, streams, events and graphs (not the workspace). */
+void ffp_batch_destroy(ffp_batch *B);
 
 /* Static text for a status code. */
 const char *ffp_strerror(int status);

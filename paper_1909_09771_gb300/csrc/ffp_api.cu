@@ -18,12 +18,10 @@ struct ffp_handle {
     KernelCtx c;
     int device;
     double *host_scal;  // pinned copy of the scalar block + flags
-    cudaEvent_t ev[3];  // preconditioner timing: start, NTD start, end
+    cudaEvent_t ev[4];  // preconditioner timing: start, B_NTD sweeps start and end, end
 };
 
-namespace {
-
-size_t prec_bytes(int prec) {
+size_t ffp::prec_bytes(int prec) {
     switch (prec) {
         case FFP_FP64: return 8;
         case FFP_FP32: return 4;
@@ -32,6 +30,7 @@ size_t prec_bytes(int prec) {
     }
 }
 
+namespace {
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 bool grid_ok(const ffp_grid *g) {
@@ -40,8 +39,11 @@ bool grid_ok(const ffp_grid *g) {
     return n <= 2000000000LL;
 }
 
-// Carve the workspace (base may be 0 to compute the size).  Returns the total size.
-size_t carve(const ffp_grid *g, int prec, char *base, Ws *ws) {
+}  // namespace
+
+// Carve the workspace (base may be 0 to compute the size) for line slot count
+// S (0: the one the grid needs).  Returns the total size.
+size_t ffp::carve_workspace(const ffp_grid *g, int prec, int S_force, char *base, Ws *ws) {
     const size_t n = (size_t)g->nx * g->ny * g->nz;
     const size_t nxy = (size_t)g->nx * g->ny;
     const size_t fb = prec_bytes(prec);
@@ -55,7 +57,7 @@ size_t carve(const ffp_grid *g, int prec, char *base, Ws *ws) {
     std::memset(&w, 0, sizeof(w));
     w.d = (double *)take(8 * n); w.cx = (double *)take(8 * n);
     w.cy = (double *)take(8 * n); w.cz = (double *)take(8 * n);
-    const int S = slots_for(g->nx);
+    const int S = S_force > 0 ? S_force : slots_for(g->nx);
     const size_t nlines = (size_t)g->ny * g->nz;
     w.rec = take(fb * nlines * (size_t)rec_len(S > 0 ? S : 1));
     w.l3 = take(fb * n);
@@ -81,6 +83,9 @@ size_t carve(const ffp_grid *g, int prec, char *base, Ws *ws) {
     return off;
 }
 
+namespace {
+size_t carve(const ffp_grid *g, int prec, char *base, Ws *ws) { return carve_workspace(g, prec, 0, base, ws); }
+
 constexpr size_t kScalBytes = 8 * (size_t)kScal + 4 * 16;
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? FFP_OK : FFP_ERR_CUDA; }
@@ -93,25 +98,24 @@ long long ntd_launches(const KernelCtx &c) {
 long long ilu_launches(const KernelCtx &c) { return 2LL * (c.ny + c.nz - 1); }
 
 // z = B^{-1} r for the handle's preconditioner (r and z distinct from c1, c2).
-// ev (optional): events recorded at the start, before the NTD sweeps and at the end.
+// ev (optional): events recorded at the start, just before and just after the
+// three B_NTD sweep launches, and at the end.
 cudaError_t precond_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
                           long long *launches, cudaEvent_t *ev = nullptr) {
     cudaError_t e = cudaSuccess;
     if (ev) e = cudaEventRecord(ev[0], st);
     if (c.precond != FFP_PRECOND_COMBO) {
-        if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-        if (e == cudaSuccess) e = launch_apply(c, r, z, st);
+        if (e == cudaSuccess) e = launch_apply(c, r, z, st, ev ? ev + 1 : nullptr);
         *launches += ntd_launches(c);
     } else {
         // B_c^{-1} r = y + B_NTD^{-1} (r - A y), y = B_ILU0^{-1} r
         if (e == cudaSuccess) e = launch_ilu_solve(c, r, c.ws.c1, st);
         if (e == cudaSuccess) e = launch_resid_vec(c, r, c.ws.c1, c.ws.c2, st);
-        if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-        if (e == cudaSuccess) e = launch_apply(c, c.ws.c2, z, st);
+        if (e == cudaSuccess) e = launch_apply(c, c.ws.c2, z, st, ev ? ev + 1 : nullptr);
         if (e == cudaSuccess) e = launch_add(c, z, c.ws.c1, st);
         *launches += ilu_launches(c) + 2 + ntd_launches(c);
     }
-    if (ev && e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+    if (ev && e == cudaSuccess) e = cudaEventRecord(ev[3], st);
     return e;
 }
 
@@ -156,7 +160,7 @@ int ffp_setup(const ffp_grid *grid, const double *kappa, const ffp_bc *bc, int f
     std::memset(h, 0, sizeof(*h));
     if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return FFP_ERR_CUDA; }
     if (cudaMallocHost((void **)&h->host_scal, kScalBytes) != cudaSuccess) { delete h; return FFP_ERR_CUDA; }
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 4; ++k)
         if (cudaEventCreate(&h->ev[k]) != cudaSuccess) { ffp_destroy(h); return FFP_ERR_CUDA; }
     KernelCtx &c = h->c;
     c.nx = grid->nx; c.ny = grid->ny; c.nz = grid->nz;
@@ -283,7 +287,7 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
         if ((status = read_scalars(h, st)) != FFP_OK) goto done;
         {
             float a = 0.f, b2 = 0.f;
-            if (cudaEventElapsedTime(&a, h->ev[0], h->ev[2]) == cudaSuccess) pre_ms += a;
+            if (cudaEventElapsedTime(&a, h->ev[0], h->ev[3]) == cudaSuccess) pre_ms += a;
             if (cudaEventElapsedTime(&b2, h->ev[1], h->ev[2]) == cudaSuccess) ntd_ms += b2;
         }
         if (host_flags(h)[FL_TIMEOUT]) { status = FFP_ERR_TIMEOUT; break; }
@@ -316,7 +320,7 @@ done:
 
 void ffp_destroy(ffp_handle *h) {
     if (!h) return;
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 4; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     if (h->host_scal) cudaFreeHost(h->host_scal);
     delete h;

@@ -39,16 +39,19 @@
 // the warp records FL_TIMEOUT and runs on without waiting, so the kernel always
 // finishes (with unusable results) instead of hanging.
 #pragma once
+#include <cstring>
+
 #include "ffp_plane.cuh"
 #include "ffp_kernels.h"
 
 namespace ffp {
 
-// Vectors are in the compute type R: FP64 for FP64 factors, FP32 otherwise
-// (the FP32 apply converts r to FP32 and z back to FP64 in GPU-wide kernels
-// around the sweeps, so no FP64 arithmetic or conversion runs inside them).
+// Typed view of one (instance, right-hand side) pair's ApplyArgs.  Vectors are
+// in the compute type R: FP64 for FP64 factors, FP32 otherwise (the FP32 apply
+// converts r to FP32 and z back to FP64 in GPU-wide kernels around the
+// sweeps, so no FP64 arithmetic or conversion runs inside them).
 template <typename F>
-struct ApplyArgs {
+struct ApplyView {
     using R = typename Compute<F>::type;
     int nx, ny, nz;
     const F *rec;  // factor line records
@@ -58,6 +61,10 @@ struct ApplyArgs {
     R *z;          // output (holds y after the lower sweeps)
     R *scr;        // 2 planes of scratch (phase 2 intermediates)
     int *flags;    // error flags (FL_TIMEOUT)
+    __device__ __forceinline__ explicit ApplyView(const ApplyArgs &a)
+        : nx(a.nx), ny(a.ny), nz(a.nz), rec(static_cast<const F *>(a.rec)),
+          l3n(static_cast<const F *>(a.l3n)), r(static_cast<const R *>(a.r)),
+          z(static_cast<R *>(a.z)), scr(static_cast<R *>(a.scr)), flags(a.flags) {}
 };
 
 __device__ __forceinline__ void cp_async_elem(float *dst, const float *src) {
@@ -98,9 +105,15 @@ struct Stage {
     static constexpr int kBytes = bytes_v(VST);
 };
 
+// One CTA per level-3 half (phases 0, 2) or per twist plane (phase 1) of one
+// pair: the pair is A0, or table[blockIdx.y] when a table is given; a pair
+// whose control word is given and has bit 0 clear returns at once.
 template <int S, typename F, int PH>
-__global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
+__global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const ApplyArgs *__restrict__ table) {
     using R = typename Compute<F>::type;
+    const ApplyArgs &src = table ? table[blockIdx.y] : A0;
+    if (src.ctl && !(*src.ctl & 1)) return;  // a batched pair that does not iterate now
+    const ApplyView<F> A(src);
     using SG = Stage<S, F, PH>;
     constexpr int NF = SG::NF, NM = SG::NM, NV = SG::NV, NST = SG::NST, D = SG::D, VST = SG::VST;
     static_assert(SG::total(NST, VST, FFP_MAX_NX) <= kSmemBudget, "stage ring does not fit");
@@ -446,42 +459,60 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs<F> A) {
 }
 
 template <int S, typename F, int PH>
-static cudaError_t launch_phase(const ApplyArgs<F> &a, int grid, cudaStream_t st) {
+static cudaError_t launch_phase(const ApplyArgs &a, const ApplyArgs *table, int nx_max, dim3 grid,
+                                cudaStream_t st) {
     using SG = Stage<S, F, PH>;
-    const size_t smem = (size_t)SG::total(SG::NST, SG::VST, a.nx);
+    const size_t smem = (size_t)SG::total(SG::NST, SG::VST, nx_max);
     cudaError_t e = cudaFuncSetAttribute(apply_kernel<S, F, PH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(apply_kernel<S, F, PH>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    apply_kernel<S, F, PH><<<grid, 128, smem, st>>>(a);
+    apply_kernel<S, F, PH><<<grid, 128, smem, st>>>(a, table);
     return cudaGetLastError();
 }
 
 template <int S, typename F>
-cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cudaStream_t st) {
+cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
+                            const cudaEvent_t *ev) {
     using R = typename Compute<F>::type;
-    ApplyArgs<F> a;
+    ApplyArgs a;
     a.nx = c.nx; a.ny = c.ny; a.nz = c.nz;
-    a.rec = (const F *)c.ws.rec;
-    a.l3n = (const F *)c.ws.l3;
-    a.scr = reinterpret_cast<R *>(c.ws.ascr);
+    a.rec = c.ws.rec;
+    a.l3n = c.ws.l3;
+    a.scr = c.ws.ascr;
     a.flags = c.ws.flags;
+    a.ctl = nullptr;
     cudaError_t e = cudaSuccess;
     if constexpr (sizeof(R) == 8) {
-        a.r = reinterpret_cast<const R *>(r);
-        a.z = reinterpret_cast<R *>(z);
+        a.r = r;
+        a.z = z;
     } else {
-        a.r = reinterpret_cast<const R *>(c.ws.r32);
-        a.z = reinterpret_cast<R *>(c.ws.z32);
+        a.r = c.ws.r32;
+        a.z = c.ws.z32;
         e = launch_to_f32(c, r, c.ws.r32, st);
     }
     const int mz = (a.nz - 1) / 2;
     const bool halves = (mz > 0) || (a.nz - 1 - mz > 0);
-    if (e == cudaSuccess && halves) e = launch_phase<S, F, 0>(a, 2, st);
-    if (e == cudaSuccess) e = launch_phase<S, F, 1>(a, 1, st);
-    if (e == cudaSuccess && halves) e = launch_phase<S, F, 2>(a, 2, st);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess && halves) e = launch_phase<S, F, 0>(a, nullptr, c.nx, dim3(2), st);
+    if (e == cudaSuccess) e = launch_phase<S, F, 1>(a, nullptr, c.nx, dim3(1), st);
+    if (e == cudaSuccess && halves) e = launch_phase<S, F, 2>(a, nullptr, c.nx, dim3(2), st);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
     if constexpr (sizeof(R) == 4) {
         if (e == cudaSuccess) e = launch_from_f32(c, c.ws.z32, z, st);
     }
+    return e;
+}
+
+// All pairs of a device table at once (vectors already in the compute type).
+template <int S, typename F>
+cudaError_t apply_table_for_slots(const ApplyArgs *table, int npairs, int nx_max, cudaStream_t st) {
+    ApplyArgs none;
+    std::memset(&none, 0, sizeof(none));
+    cudaError_t e = launch_phase<S, F, 0>(none, table, nx_max, dim3(2, npairs), st);
+    if (e == cudaSuccess) e = launch_phase<S, F, 1>(none, table, nx_max, dim3(1, npairs), st);
+    if (e == cudaSuccess) e = launch_phase<S, F, 2>(none, table, nx_max, dim3(2, npairs), st);
     return e;
 }
 

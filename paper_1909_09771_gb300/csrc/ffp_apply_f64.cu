@@ -3,7 +3,8 @@
 #include "ffp_apply.cuh"
 
 namespace ffp {
-#define FFP_INST(SS) template cudaError_t apply_for_slots<SS, double>(const KernelCtx &, const double *, double *, cudaStream_t);
+#define FFP_INST(SS) template cudaError_t apply_for_slots<SS, double>(const KernelCtx &, const double *, double *, cudaStream_t, const cudaEvent_t *); \
+    template cudaError_t apply_table_for_slots<SS, double>(const ApplyArgs *, int, int, cudaStream_t);
 FFP_SLOT_LIST(FFP_INST)
 #undef FFP_INST
 }  // namespace ffp

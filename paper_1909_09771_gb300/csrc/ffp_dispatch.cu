@@ -7,8 +7,12 @@
 namespace ffp {
 
 template <int S> cudaError_t setup_for_slots(const KernelCtx &, const double *, cudaStream_t);
+template <int S> cudaError_t setup_table_for_slots(const SetupArgs *, int, int, cudaStream_t);
 template <int S, typename F>
-cudaError_t apply_for_slots(const KernelCtx &, const double *, double *, cudaStream_t);
+cudaError_t apply_for_slots(const KernelCtx &, const double *, double *, cudaStream_t,
+                            const cudaEvent_t *);
+template <int S, typename F>
+cudaError_t apply_table_for_slots(const ApplyArgs *, int, int, cudaStream_t);
 
 cudaError_t launch_setup(const KernelCtx &c, const double *t, cudaStream_t st) {
     switch (c.slots) {
@@ -19,21 +23,53 @@ cudaError_t launch_setup(const KernelCtx &c, const double *t, cudaStream_t st) {
     }
 }
 
-template <typename F>
-static cudaError_t apply_t(const KernelCtx &c, const double *r, double *z, cudaStream_t st) {
-    switch (c.slots) {
-#define FFP_CASE(SS) case SS: return apply_for_slots<SS, F>(c, r, z, st);
+cudaError_t launch_setup_table(int slots, const SetupArgs *table, int count, int nx_max,
+                               cudaStream_t st) {
+    switch (slots) {
+#define FFP_CASE(SS) case SS: return setup_table_for_slots<SS>(table, count, nx_max, st);
         FFP_SLOT_LIST(FFP_CASE)
 #undef FFP_CASE
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st) {
+template <typename F>
+static cudaError_t apply_t(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
+                           const cudaEvent_t *ev) {
+    switch (c.slots) {
+#define FFP_CASE(SS) case SS: return apply_for_slots<SS, F>(c, r, z, st, ev);
+        FFP_SLOT_LIST(FFP_CASE)
+#undef FFP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
+                         const cudaEvent_t *ev) {
     switch (c.prec) {
-        case FFP_FP64: return apply_t<double>(c, r, z, st);
-        case FFP_FP32: return apply_t<float>(c, r, z, st);
-        case FFP_BF16: return apply_t<__nv_bfloat16>(c, r, z, st);
+        case FFP_FP64: return apply_t<double>(c, r, z, st, ev);
+        case FFP_FP32: return apply_t<float>(c, r, z, st, ev);
+        case FFP_BF16: return apply_t<__nv_bfloat16>(c, r, z, st, ev);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename F>
+static cudaError_t apply_table_t(int slots, const ApplyArgs *t, int n, int nxm, cudaStream_t st) {
+    switch (slots) {
+#define FFP_CASE(SS) case SS: return apply_table_for_slots<SS, F>(t, n, nxm, st);
+        FFP_SLOT_LIST(FFP_CASE)
+#undef FFP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_apply_table(int prec, int slots, const ApplyArgs *table, int npairs, int nx_max,
+                               cudaStream_t st) {
+    switch (prec) {
+        case FFP_FP64: return apply_table_t<double>(slots, table, npairs, nx_max, st);
+        case FFP_FP32: return apply_table_t<float>(slots, table, npairs, nx_max, st);
+        case FFP_BF16: return apply_table_t<__nv_bfloat16>(slots, table, npairs, nx_max, st);
         default: return cudaErrorInvalidValue;
     }
 }

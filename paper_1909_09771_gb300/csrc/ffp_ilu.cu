@@ -13,6 +13,8 @@
 // is first order: an affine map per cell (triangular sweeps) or a Moebius map
 // (pivots), evaluated as lane-local composition + a 32-lane scan + lane-local
 // substitution, lane l holding cells l*S .. l*S+S-1.
+#include <cstring>
+
 #include "ffp_kernels.h"
 
 namespace ffp {
@@ -44,13 +46,17 @@ __device__ __forceinline__ bool diag_line(const IluGeo &g, int s, int j, int &y,
 // e_a = A[a-1, a] (0 at x = 0 or across the block split).  Projective scan as
 // in twisted_pivots, over one 32-lane chain.
 template <int S>
-__global__ void __launch_bounds__(128) ilu_pivot_kernel(int nx, int ny, int nz, int s,
-                                                        const double *__restrict__ d,
-                                                        const double *__restrict__ cx,
-                                                        const double *__restrict__ cy,
-                                                        const double *__restrict__ cz,
-                                                        double *D64, void *dinv, int prec,
-                                                        int *flags) {
+__global__ void __launch_bounds__(128) ilu_pivot_kernel(IluPivArgs P0,
+                                                        const IluPivArgs *__restrict__ table, int s) {
+    const IluPivArgs &P = table ? table[blockIdx.y] : P0;
+    const int nx = P.nx, ny = P.ny, nz = P.nz, prec = P.prec;
+    const double *__restrict__ d = P.d;
+    const double *__restrict__ cx = P.cx;
+    const double *__restrict__ cy = P.cy;
+    const double *__restrict__ cz = P.cz;
+    double *D64 = P.D64;
+    void *dinv = P.dinv;
+    int *flags = P.flags;
     const IluGeo g = ilu_geo(nx, ny, nz);
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -126,18 +132,31 @@ __global__ void __launch_bounds__(128) ilu_pivot_kernel(int nx, int ny, int nz, 
 }
 
 // ---------------------------------------------------------------- triangular sweeps
+// Typed view of one pair's IluArgs.
 template <typename F>
-struct IluArgs {
+struct IluView {
     int nx, ny, nz;
-    const F *dinv, *lx, *ly, *lz;  // 1/D and the x, y, z bands of A in storage precision
+    const F *dinv, *lx, *ly, *lz;
     const double *r;
-    double *t;  // forward result, then overwritten by the backward result
+    double *t;
+    __device__ __forceinline__ explicit IluView(const IluArgs &a)
+        : nx(a.nx), ny(a.ny), nz(a.nz), dinv(static_cast<const F *>(a.dinv)),
+          lx(static_cast<const F *>(a.lx)), ly(static_cast<const F *>(a.ly)),
+          lz(static_cast<const F *>(a.lz)), r(a.r), t(a.t) {}
 };
 
-// forward: t_a = dinv_a (r_a - ly t_{a-nx} - lz t_{a-nxy} - lx_{a-1} t_{a-1})
+// The pair of this CTA (A0, or table[blockIdx.y]); false if it is skipped.
+__device__ __forceinline__ bool ilu_pair(const IluArgs &A0, const IluArgs *table, IluArgs &A) {
+    A = table ? table[blockIdx.y] : A0;
+    return !A.ctl || (*A.ctl & 1);
+}
+
 template <int S, typename F>
-__global__ void __launch_bounds__(128) ilu_fwd_kernel(IluArgs<F> A, int s) {
+__global__ void __launch_bounds__(256) ilu_fwd_kernel(IluArgs A0, const IluArgs *__restrict__ table, int s) {
     using R = typename Compute<F>::type;
+    IluArgs a0;
+    if (!ilu_pair(A0, table, a0)) return;
+    const IluView<F> A(a0);
     const IluGeo g = ilu_geo(A.nx, A.ny, A.nz);
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -183,8 +202,11 @@ __global__ void __launch_bounds__(128) ilu_fwd_kernel(IluArgs<F> A, int s) {
 
 // backward: z_a = t_a - dinv_a (lx_a z_{a+1} + ly_a z_{a+nx} + lz_a z_{a+nxy}), in place on t
 template <int S, typename F>
-__global__ void __launch_bounds__(128) ilu_bwd_kernel(IluArgs<F> A, int s) {
+__global__ void __launch_bounds__(256) ilu_bwd_kernel(IluArgs A0, const IluArgs *__restrict__ table, int s) {
     using R = typename Compute<F>::type;
+    IluArgs a0;
+    if (!ilu_pair(A0, table, a0)) return;
+    const IluView<F> A(a0);
     const IluGeo g = ilu_geo(A.nx, A.ny, A.nz);
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -237,32 +259,66 @@ static int diag_len(int ny, int nz, int s) {
 
 template <int S>
 static cudaError_t ilu_setup_s(const KernelCtx &c, double *D64, cudaStream_t st) {
+    IluPivArgs a;
+    a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.prec = c.prec;
+    a.d = c.ws.d; a.cx = c.ws.cx; a.cy = c.ws.cy; a.cz = c.ws.cz;
+    a.D64 = D64; a.dinv = c.ws.dinv; a.flags = c.ws.flags;
     const int nd = c.ny + c.nz - 1;
     for (int s = 0; s < nd; ++s) {
         const int lines = diag_len(c.ny, c.nz, s);
-        ilu_pivot_kernel<S><<<(lines + 3) / 4, 128, 0, st>>>(c.nx, c.ny, c.nz, s, c.ws.d, c.ws.cx,
-                                                             c.ws.cy, c.ws.cz, D64, c.ws.dinv,
-                                                             c.prec, c.ws.flags);
+        ilu_pivot_kernel<S><<<(lines + 3) / 4, 128, 0, st>>>(a, nullptr, s);
+    }
+    return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t ilu_setup_table_s(const IluPivArgs *table, int count, int ndiag, int maxlines,
+                                     cudaStream_t st) {
+    IluPivArgs none;
+    std::memset(&none, 0, sizeof(none));
+    for (int s = 0; s < ndiag; ++s)
+        ilu_pivot_kernel<S><<<dim3((maxlines + 3) / 4, count), 128, 0, st>>>(none, table, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ilu_setup_table(int slots, const IluPivArgs *table, int count, int ndiag,
+                                   int maxlines, cudaStream_t st) {
+    if (count < 1 || ndiag < 1 || maxlines < 1) return cudaErrorInvalidValue;
+    switch (slots) {
+#define FFP_CASE(SS) case SS: return ilu_setup_table_s<SS>(table, count, ndiag, maxlines, st);
+        FFP_SLOT_LIST(FFP_CASE)
+#undef FFP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int S, typename F>
+static cudaError_t ilu_solve_s(const KernelCtx &c, const double *r, double *t, cudaStream_t st) {
+    IluArgs a;
+    a.nx = c.nx; a.ny = c.ny; a.nz = c.nz;
+    a.dinv = c.ws.dinv; a.lx = c.ws.lx; a.ly = c.ws.ly; a.lz = c.ws.l3;
+    a.r = r; a.t = t;
+    a.ctl = nullptr;
+    const int nd = c.ny + c.nz - 1;
+    for (int s = 0; s < nd; ++s) {
+        const int lines = diag_len(c.ny, c.nz, s);
+        ilu_fwd_kernel<S, F><<<(lines + 3) / 4, 128, 0, st>>>(a, nullptr, s);
+    }
+    for (int s = nd - 1; s >= 0; --s) {
+        const int lines = diag_len(c.ny, c.nz, s);
+        ilu_bwd_kernel<S, F><<<(lines + 3) / 4, 128, 0, st>>>(a, nullptr, s);
     }
     return cudaGetLastError();
 }
 
 template <int S, typename F>
-static cudaError_t ilu_solve_s(const KernelCtx &c, const double *r, double *t, cudaStream_t st) {
-    IluArgs<F> a;
-    a.nx = c.nx; a.ny = c.ny; a.nz = c.nz;
-    a.dinv = (const F *)c.ws.dinv; a.lx = (const F *)c.ws.lx; a.ly = (const F *)c.ws.ly;
-    a.lz = (const F *)c.ws.l3;
-    a.r = r; a.t = t;
-    const int nd = c.ny + c.nz - 1;
-    for (int s = 0; s < nd; ++s) {
-        const int lines = diag_len(c.ny, c.nz, s);
-        ilu_fwd_kernel<S, F><<<(lines + 3) / 4, 128, 0, st>>>(a, s);
-    }
-    for (int s = nd - 1; s >= 0; --s) {
-        const int lines = diag_len(c.ny, c.nz, s);
-        ilu_bwd_kernel<S, F><<<(lines + 3) / 4, 128, 0, st>>>(a, s);
-    }
+static cudaError_t ilu_table_s(const IluArgs *table, int npairs, int ndiag, int maxlines, int warps,
+                               cudaStream_t st) {
+    IluArgs none;
+    std::memset(&none, 0, sizeof(none));
+    const dim3 grid((maxlines + warps - 1) / warps, npairs);
+    for (int s = 0; s < ndiag; ++s) ilu_fwd_kernel<S, F><<<grid, 32 * warps, 0, st>>>(none, table, s);
+    for (int s = ndiag - 1; s >= 0; --s) ilu_bwd_kernel<S, F><<<grid, 32 * warps, 0, st>>>(none, table, s);
     return cudaGetLastError();
 }
 
@@ -298,6 +354,27 @@ cudaError_t launch_ilu_solve(const KernelCtx &c, const double *r, double *t, cud
         case FFP_FP64: return ilu_solve_t<double>(c, r, t, st);
         case FFP_FP32: return ilu_solve_t<float>(c, r, t, st);
         case FFP_BF16: return ilu_solve_t<__nv_bfloat16>(c, r, t, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename F>
+static cudaError_t ilu_table_t(int slots, const IluArgs *t, int np, int nd, int ml, int w, cudaStream_t st) {
+    switch (slots) {
+#define FFP_CASE(SS) case SS: return ilu_table_s<SS, F>(t, np, nd, ml, w, st);
+        FFP_SLOT_LIST(FFP_CASE)
+#undef FFP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_ilu_table(int prec, int slots, const IluArgs *table, int npairs, int ndiag,
+                             int maxlines, int warps, cudaStream_t st) {
+    if (npairs < 1 || ndiag < 1 || maxlines < 1 || warps < 1 || warps > 8) return cudaErrorInvalidValue;
+    switch (prec) {
+        case FFP_FP64: return ilu_table_t<double>(slots, table, npairs, ndiag, maxlines, warps, st);
+        case FFP_FP32: return ilu_table_t<float>(slots, table, npairs, ndiag, maxlines, warps, st);
+        case FFP_BF16: return ilu_table_t<__nv_bfloat16>(slots, table, npairs, ndiag, maxlines, warps, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -18,6 +18,11 @@ struct KernelCtx {
     Ws ws;
 };
 
+// ffp_api.cu: bytes per stored factor value, and the workspace layout (base may
+// be null to size it; S_force > 0 forces the line slot count)
+size_t prec_bytes(int prec);
+size_t carve_workspace(const ffp_grid *g, int prec, int S_force, char *base, Ws *ws);
+
 // ffp_ops.cu
 cudaError_t launch_assemble(const KernelCtx &c, const double *kappa, const unsigned char bc[6],
                             cudaStream_t st);
@@ -45,11 +50,80 @@ cudaError_t launch_finalize(const KernelCtx &c, int mode, int fresh, int flexibl
 // ffp_setup.cu
 cudaError_t launch_setup(const KernelCtx &c, const double *t, cudaStream_t st);
 
-// ffp_dispatch.cu: z = B_NTD^{-1} r
-cudaError_t launch_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st);
+// One instance of the setup kernels.
+struct SetupArgs {
+    int nx, ny, nz;
+    int prec;  // storage precision of the factor records
+    const double *d, *cx, *cy, *cz;
+    const double *t;  // filter, NULL = rowsum
+    void *rec;        // factor line records (rec_len(S) entries per line)
+    void *l1n;        // natural-order x-band of T (for export)
+    Ws ws;
+};
+
+inline void fill_setup_args(const KernelCtx &c, const double *t, SetupArgs *a) {
+    a->nx = c.nx; a->ny = c.ny; a->nz = c.nz; a->prec = c.prec;
+    a->d = c.ws.d; a->cx = c.ws.cx; a->cy = c.ws.cy; a->cz = c.ws.cz;
+    a->t = t;
+    a->rec = c.ws.rec;
+    a->l1n = c.ws.l1;
+    a->ws = c.ws;
+}
+
+// ffp_dispatch.cu: setup of every instance of a device table whose lines all use `slots`
+cudaError_t launch_setup_table(int slots, const SetupArgs *table, int count, int nx_max,
+                               cudaStream_t st);
+
+// One (instance, right-hand side) pair of the NTD apply.  Vectors r, z, scr are
+// in the compute type (FP64 for FP64 factors, FP32 otherwise).
+struct ApplyArgs {
+    int nx, ny, nz;
+    const void *rec;  // factor line records
+    const void *l3n;  // natural-order z-band
+    const void *r;
+    void *z;
+    void *scr;        // 2 planes
+    int *flags;
+    const int *ctl;   // batched solves: the pair is skipped unless *ctl & 1 (null: always run)
+};
+
+// ffp_dispatch.cu: NTD apply of every pair of a device table (one launch per phase)
+cudaError_t launch_apply_table(int prec, int slots, const ApplyArgs *table, int npairs, int nx_max,
+                               cudaStream_t st);
+
+// ffp_dispatch.cu: z = B_NTD^{-1} r; ev (optional) = two events recorded just
+// before and just after the three sweep launches
+cudaError_t launch_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
+                         const cudaEvent_t *ev = nullptr);
 
 // ffp_ilu.cu: ILU(0) of blkD(A) (pivots in D64 scratch, 1/D stored) and t = B_ILU0^{-1} r
 cudaError_t launch_ilu_setup(const KernelCtx &c, double *D64, cudaStream_t st);
+
+// One instance of the ILU(0) pivot wavefront.
+struct IluPivArgs {
+    int nx, ny, nz, prec;
+    const double *d, *cx, *cy, *cz;
+    double *D64;  // FP64 pivots (scratch)
+    void *dinv;   // 1/D in storage precision
+    int *flags;
+};
+cudaError_t launch_ilu_setup_table(int slots, const IluPivArgs *table, int count, int ndiag,
+                                   int maxlines, cudaStream_t st);
 cudaError_t launch_ilu_solve(const KernelCtx &c, const double *r, double *t, cudaStream_t st);
+int ilu_slots(int nx);  // lane split of the ILU(0) line sweeps
+
+// One pair of the ILU(0) solve t = B_ILU0^{-1} r; factors in storage precision.
+struct IluArgs {
+    int nx, ny, nz;
+    const void *dinv, *lx, *ly, *lz;  // 1/D and the x, y, z bands of A
+    const double *r;
+    double *t;
+    const int *ctl;  // the pair is skipped unless *ctl & 1 (null: always run)
+};
+// ILU(0) solves of every pair of a device table whose lines all use `slots`
+// (ndiag, maxlines: the largest wavefront length and diagonal of the pairs;
+// warps: lines per CTA)
+cudaError_t launch_ilu_table(int prec, int slots, const IluArgs *table, int npairs, int ndiag,
+                             int maxlines, int warps, cudaStream_t st);
 
 }  // namespace ffp

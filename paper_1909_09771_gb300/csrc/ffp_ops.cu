@@ -7,17 +7,9 @@
 // SpMV (Sec. II band storage): y_a = d_a x_a + sum of the six couplings.
 // Reductions are deterministic: a fixed grid, a fixed per-block tree and a
 // fixed-order final sum in finalize_kernel.
-#include "ffp_kernels.h"
+#include "ffp_vecops.cuh"
 
 namespace ffp {
-
-constexpr int kThreads = 256;
-
-struct Geo {
-    int nx, ny, nz;
-    long long n;
-    int nxy;
-};
 
 __device__ __forceinline__ double harmonic(double ka, double kb) { return 2.0 * ka * kb / (ka + kb); }
 
@@ -98,25 +90,6 @@ __global__ void export_rec_kernel(Geo g, int S, const F *__restrict__ rec, int w
     }
 }
 
-// (A x)_a with the oracle's term order.
-__device__ __forceinline__ double stencil(const Geo &g, long long a, const double *__restrict__ d,
-                                          const double *__restrict__ cx,
-                                          const double *__restrict__ cy,
-                                          const double *__restrict__ cz,
-                                          const double *__restrict__ x) {
-    const int ix = (int)(a % g.nx);
-    const int iy = (int)((a / g.nx) % g.ny);
-    const int iz = (int)(a / g.nxy);
-    double s = d[a] * x[a];
-    if (ix > 0) s += cx[a - 1] * x[a - 1];
-    if (ix + 1 < g.nx) s += cx[a] * x[a + 1];
-    if (iy > 0) s += cy[a - g.nx] * x[a - g.nx];
-    if (iy + 1 < g.ny) s += cy[a] * x[a + g.nx];
-    if (iz > 0) s += cz[a - g.nxy] * x[a - g.nxy];
-    if (iz + 1 < g.nz) s += cz[a] * x[a + g.nxy];
-    return s;
-}
-
 __global__ void __launch_bounds__(kThreads) spmv_kernel(Geo g, const double *__restrict__ d,
                                                        const double *__restrict__ cx,
                                                        const double *__restrict__ cy,
@@ -159,29 +132,6 @@ __global__ void __launch_bounds__(kThreads) from_f32_kernel(long long n, const f
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x)
         y[a] = (double)x[a];
-}
-
-// Block sum of NV values per thread, written to red[blockIdx.x * NV + v], fixed order.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double *red) {
-    __shared__ double sh[NV][kThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double s = v[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) sh[k][wid] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) s += sh[k][w];
-            red[blockIdx.x * NV + k] = s;
-        }
-    }
 }
 
 // r = b - A x ; partials (r.r, b.b)
@@ -265,50 +215,10 @@ __global__ void __launch_bounds__(kThreads) update_p_kernel(long long n,
         p[a] = fresh ? z[a] : z[a] + beta * p[a];
 }
 
-// Sum of red[i*stride + k], i < nblk, by one warp in a fixed order (lane-strided
-// partial sums, then a fixed shuffle tree); every lane gets the result.
-__device__ __forceinline__ double warp_fold(const double *__restrict__ red, int nblk, int stride,
-                                            int k) {
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int i = lane; i < nblk; i += 32) s += red[i * stride + k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
-}
-
 // Fold the partial sums and update the CG scalars (one warp).
 __global__ void finalize_kernel(int mode, int nblk, int fresh, int flexible,
                                 const double *__restrict__ red, double *scal, int *flags) {
-    if (mode == FIN_RESID) {
-        const double rr = warp_fold(red, nblk, 2, 0);
-        const double bb = warp_fold(red, nblk, 2, 1);
-        if (threadIdx.x == 0) { scal[SC_TRR] = rr; scal[SC_RR] = rr; scal[SC_BB] = bb; }
-    } else if (mode == FIN_PQ) {
-        const double pq = warp_fold(red, nblk, 1, 0);
-        if (threadIdx.x == 0) {
-            scal[SC_PQ] = pq;
-            if (!(pq > 0.0) || !isfinite(pq)) flags[FL_PQ] = 1;
-            scal[SC_ALPHA] = scal[SC_RHO] / pq;
-        }
-    } else if (mode == FIN_RR) {
-        const double rr = warp_fold(red, nblk, 1, 0);
-        if (threadIdx.x == 0) scal[SC_RR] = rr;
-    } else {
-        const double rz = warp_fold(red, nblk, 2, 0);
-        const double zq = warp_fold(red, nblk, 2, 1);
-        if (threadIdx.x == 0) {
-            double beta = 0.0;
-            if (!fresh) {
-                if (flexible) beta = -scal[SC_ALPHA] * zq / scal[SC_RHO];  // (z, r_new - r_old) / rho
-                else beta = rz / scal[SC_RHO];
-            }
-            scal[SC_BETA] = beta;
-            scal[SC_ZQ] = zq;
-            scal[SC_RHO_OLD] = scal[SC_RHO];
-            scal[SC_RHO] = rz;
-        }
-    }
+    finalize_scalars(mode, nblk, fresh, flexible, red, scal, flags);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -318,12 +228,6 @@ static Geo geo(const KernelCtx &c) {
     return g;
 }
 
-static int grid_for(long long n) {
-    long long b = (n + kThreads - 1) / kThreads;
-    if (b > kRedBlocks) b = kRedBlocks;
-    if (b < 1) b = 1;
-    return (int)b;
-}
 
 cudaError_t launch_assemble(const KernelCtx &c, const double *kappa, const unsigned char bc[6],
                             cudaStream_t st) {
@@ -343,7 +247,6 @@ cudaError_t launch_check_filter(const KernelCtx &c, const double *t, cudaStream_
 }
 
 static Geo geo(const KernelCtx &c);
-static int grid_for(long long n);
 
 template <typename F>
 static void convert_all(const KernelCtx &c, cudaStream_t st) {

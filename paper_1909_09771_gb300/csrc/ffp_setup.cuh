@@ -20,20 +20,12 @@
 // Stored: l1 = x-band of T_k, minv = 1/M, l2 = y-band of P_i (l3 = z-band of A
 // is converted separately).
 #pragma once
+#include <cstring>
+
 #include "ffp_plane.cuh"
 #include "ffp_kernels.h"
 
 namespace ffp {
-
-struct SetupArgs {
-    int nx, ny, nz;
-    int prec;  // storage precision of the factor records
-    const double *d, *cx, *cy, *cz;
-    const double *t;  // filter, NULL = rowsum
-    void *rec;        // factor line records (rec_len(S) entries per line)
-    void *l1n;        // natural-order x-band of T (for export)
-    Ws ws;
-};
 
 // Store one factor entry in the storage precision.
 __device__ __forceinline__ void put_factor(void *base, long idx, double v, int prec) {
@@ -279,7 +271,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
 }
 
 template <int S>
-__global__ void __launch_bounds__(256) setup_kernel(SetupArgs A, int phase) {
+__device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
     extern __shared__ __align__(16) double sm[];
     const int nx = A.nx, ny = A.ny, nz = A.nz;
     const long nxy = (long)nx * ny;
@@ -376,21 +368,39 @@ __global__ void __launch_bounds__(256) setup_kernel(SetupArgs A, int phase) {
     }
 }
 
+// Phase 0: one CTA per level-3 half; phase 1: the twist plane.  The instance
+// is A0, or table[blockIdx.y] when a table is given.
+template <int S>
+__global__ void __launch_bounds__(256) setup_kernel(const __grid_constant__ SetupArgs A0,
+                                                    const SetupArgs *__restrict__ table, int phase) {
+    const SetupArgs &A = table ? table[blockIdx.y] : A0;
+    if (phase == 0 && A.nz <= 1) return;  // a single plane has no level-3 halves
+    setup_body<S>(A, phase);
+}
+
+template <int S>
+cudaError_t setup_table_for_slots(const SetupArgs *table, int count, int nx_max, cudaStream_t st) {
+    const size_t smem = sizeof(double) * 14 * (size_t)nx_max;
+    cudaError_t e = cudaFuncSetAttribute(setup_kernel<S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    SetupArgs none;
+    std::memset(&none, 0, sizeof(none));
+    setup_kernel<S><<<dim3(2, count), 256, smem, st>>>(none, table, 0);
+    setup_kernel<S><<<dim3(1, count), 256, smem, st>>>(none, table, 1);
+    return cudaGetLastError();
+}
+
 template <int S>
 cudaError_t setup_for_slots(const KernelCtx &c, const double *t, cudaStream_t st) {
     SetupArgs a;
-    a.nx = c.nx; a.ny = c.ny; a.nz = c.nz; a.prec = c.prec;
-    a.d = c.ws.d; a.cx = c.ws.cx; a.cy = c.ws.cy; a.cz = c.ws.cz;
-    a.t = t;
-    a.rec = c.ws.rec;
-    a.l1n = c.ws.l1;
-    a.ws = c.ws;
+    fill_setup_args(c, t, &a);
     const size_t smem = sizeof(double) * 14 * (size_t)a.nx;
     cudaError_t e = cudaFuncSetAttribute(setup_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    if (a.nz > 1) setup_kernel<S><<<2, 256, smem, st>>>(a, 0);
-    setup_kernel<S><<<1, 256, smem, st>>>(a, 1);
+    if (a.nz > 1) setup_kernel<S><<<2, 256, smem, st>>>(a, nullptr, 0);
+    setup_kernel<S><<<1, 256, smem, st>>>(a, nullptr, 1);
     return cudaGetLastError();
 }
 

@@ -3,7 +3,9 @@
 #include "ffp_setup.cuh"
 
 namespace ffp {
-#define X(SS) template cudaError_t setup_for_slots<SS>(const KernelCtx &, const double *, cudaStream_t);
+#define X(SS)                                                                                   \
+    template cudaError_t setup_for_slots<SS>(const KernelCtx &, const double *, cudaStream_t); \
+    template cudaError_t setup_table_for_slots<SS>(const SetupArgs *, int, int, cudaStream_t);
 X(1) X(2) X(3) X(4) X(6)
 #undef X
 }  // namespace ffp

@@ -3,7 +3,9 @@
 #include "ffp_setup.cuh"
 
 namespace ffp {
-#define X(SS) template cudaError_t setup_for_slots<SS>(const KernelCtx &, const double *, cudaStream_t);
-X(22) X(32)
+#define X(SS)                                                                                   \
+    template cudaError_t setup_for_slots<SS>(const KernelCtx &, const double *, cudaStream_t); \
+    template cudaError_t setup_table_for_slots<SS>(const SetupArgs *, int, int, cudaStream_t);
+X(22)
 #undef X
 }  // namespace ffp

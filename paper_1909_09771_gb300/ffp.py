@@ -53,6 +53,17 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("ilu_warps", ctypes.c_int), ("branches", ctypes.c_int), ("ms", ctypes.c_double),
+                ("ntd_ms", ctypes.c_double), ("from_cache", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+FFP_BATCH_MAX_PAIRS = 65535
+
+
 class FFPError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -89,7 +100,22 @@ def load():
     lib.ffp_destroy.restype = None
     lib.ffp_strerror.argtypes = [ctypes.c_int]
     lib.ffp_strerror.restype = ctypes.c_char_p
-    for f in (lib.ffp_setup, lib.ffp_spmv, lib.ffp_apply, lib.ffp_pcg_solve, lib.ffp_export):
+    lib.ffp_apply_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.ffp_batch_workspace_bytes.argtypes = [ctypes.c_int, P(Grid), ctypes.c_int, ctypes.c_int]
+    lib.ffp_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.ffp_batch_setup.argtypes = [ctypes.c_int, P(Grid), P(vp), P(BC), P(vp), ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, vp, P(vp)]
+    lib.ffp_batch_tune.argtypes = [vp, ctypes.c_char_p, P(BatchConfig), vp]
+    lib.ffp_batch_get_config.argtypes = [vp, P(BatchConfig)]
+    lib.ffp_batch_set_config.argtypes = [vp, P(BatchConfig)]
+    lib.ffp_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_longlong),
+                                   P(ctypes.c_longlong)]
+    lib.ffp_batch_solve.argtypes = [vp, P(vp), P(vp), ctypes.c_double, ctypes.c_int, P(Stats), vp]
+    lib.ffp_batch_destroy.argtypes = [vp]
+    lib.ffp_batch_destroy.restype = None
+    for f in (lib.ffp_setup, lib.ffp_spmv, lib.ffp_apply, lib.ffp_pcg_solve, lib.ffp_export,
+              lib.ffp_apply_noalloc, lib.ffp_batch_setup, lib.ffp_batch_tune, lib.ffp_batch_get_config,
+              lib.ffp_batch_set_config, lib.ffp_batch_info, lib.ffp_batch_solve):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -134,7 +160,7 @@ def setup_launches(grid, precond="ntd", user_t=False):
     """Kernels one ffp_setup launches (assembly, filter check, band conversion,
     setup phases, ILU(0) pivot diagonals)."""
     nx, ny, nz = grid
-    n = 1 + (1 if user_t else 0) + (3 if precond == "combo" else 1) + (2 if nz > 1 else 1)
+    n = 1 + (1 if user_t else 0) + (4 if precond == "combo" else 2) + (2 if nz > 1 else 1)
     return n + ((ny + nz - 1) if precond == "combo" else 0)
 
 
@@ -225,3 +251,122 @@ class Preconditioner:
         if st != FFP_OK:
             raise FFPError(st, "ffp_export")
         return out
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for k, t in enumerate(tensors):
+        arr[k] = None if t is None else t.data_ptr()
+    return arr
+
+
+def batch_workspace_bytes(grids, nrhs, precision="fp32", lengths=None):
+    g = (Grid * len(grids))(*[_grid(gr, (lengths[k] if lengths else (1.0, 1.0, 1.0)))
+                             for k, gr in enumerate(grids)])
+    return int(load().ffp_batch_workspace_bytes(len(grids), g, int(nrhs), PRECISIONS[precision]))
+
+
+class Batch:
+    """Many independent instances (own grid, kappa, boundary conditions and
+    preconditioner) with nrhs right-hand sides each, solved together
+    (ffp_batch_* in include/ffp.h).  Pairs are numbered i * nrhs + j."""
+
+    def __init__(self, grids, kappas, bcs, nrhs=1, precision="fp32", precond="combo", ts=None,
+                 lengths=None, stream=None, workspace=None):
+        lib = load()
+        self.grids = [tuple(int(v) for v in g) for g in grids]
+        self.count = len(self.grids)
+        self.nrhs = int(nrhs)
+        self.n = [g[0] * g[1] * g[2] for g in self.grids]
+        self.precision, self.precond = precision, precond
+        self._g = (Grid * self.count)(*[_grid(gr, (lengths[k] if lengths else (1.0, 1.0, 1.0)))
+                                        for k, gr in enumerate(self.grids)])
+        nbytes = lib.ffp_batch_workspace_bytes(self.count, self._g, self.nrhs, PRECISIONS[precision])
+        if nbytes == 0:
+            raise FFPError(FFP_ERR_ARG, "ffp_batch_workspace_bytes")
+        kappas = [_dev_vec(k, self.n[i], f"kappa[{i}]") for i, k in enumerate(kappas)]
+        dev = kappas[0].device
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        elif not (workspace.is_cuda and workspace.dtype == torch.uint8 and workspace.numel() >= nbytes
+                  and workspace.data_ptr() % 256 == 0):
+            raise ValueError(f"workspace must be a 256-byte aligned CUDA uint8 tensor of >= {nbytes} bytes")
+        self.workspace = workspace
+        self.workspace_bytes = nbytes
+        if ts is not None:
+            ts = [None if t is None else _dev_vec(t, self.n[i], f"t[{i}]") for i, t in enumerate(ts)]
+        self._keep = (kappas, ts)
+        bca = (BC * self.count)(*[BC((ctypes.c_ubyte * 6)(*[int(v) for v in bc])) for bc in bcs])
+        h = ctypes.c_void_p()
+        st = lib.ffp_batch_setup(self.count, self._g, _ptr_array(kappas), bca,
+                                 _ptr_array(ts) if ts is not None else None, self.nrhs,
+                                 PRECISIONS[precision], PRECONDS[precond], _ptr(self.workspace),
+                                 ctypes.c_size_t(nbytes), _stream(stream), ctypes.byref(h))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_batch_setup")
+        self._h = h
+
+    @property
+    def npairs(self):
+        return self.count * self.nrhs
+
+    def pair_size(self, p):
+        return self.n[p // self.nrhs]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ffp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, cache_path=None, stream=None):
+        c = BatchConfig()
+        st = load().ffp_batch_tune(self._h, cache_path.encode() if cache_path else None,
+                                   ctypes.byref(c), _stream(stream))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_batch_tune")
+        return c.as_dict()
+
+    def config(self):
+        c = BatchConfig()
+        st = load().ffp_batch_get_config(self._h, ctypes.byref(c))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_batch_get_config")
+        return c.as_dict()
+
+    def set_config(self, ilu_warps, branches):
+        c = BatchConfig(int(ilu_warps), int(branches), 0.0, 0.0, 0)
+        st = load().ffp_batch_set_config(self._h, ctypes.byref(c))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_batch_set_config")
+
+    def info(self):
+        ng, npair, nl, ns = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        st = load().ffp_batch_info(self._h, ctypes.byref(ng), ctypes.byref(npair), ctypes.byref(nl),
+                                   ctypes.byref(ns))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_batch_info")
+        return {"groups": ng.value, "pairs": npair.value, "launches_per_iter": nl.value,
+                "setup_launches": ns.value}
+
+    def solve(self, bs, xs=None, rtol=1e-8, maxit=200, stream=None, check=True):
+        """Solve every pair; bs, xs: lists of count * nrhs CUDA float64 tensors
+        (xs, if given, hold x0 and receive the solutions).  Returns (xs, stats)."""
+        if len(bs) != self.npairs:
+            raise ValueError(f"need {self.npairs} right-hand sides")
+        bs = [_dev_vec(b, self.pair_size(p), f"b[{p}]") for p, b in enumerate(bs)]
+        if xs is None:
+            xs = [torch.zeros_like(b) for b in bs]
+        else:
+            xs = [_dev_vec(x, self.pair_size(p), f"x[{p}]") for p, x in enumerate(xs)]
+        stats = (Stats * self.npairs)()
+        st = load().ffp_batch_solve(self._h, _ptr_array(bs), _ptr_array(xs), float(rtol), int(maxit),
+                                    stats, _stream(stream))
+        if check and st != FFP_OK:
+            raise FFPError(st, "ffp_batch_solve")
+        return xs, [s.as_dict() for s in stats]
