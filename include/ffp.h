@@ -270,6 +270,79 @@ int ffp_batch_solve(ffp_batch *B, const double *const *b, double *const *x, doub
 /* Free the batch's host state, streams, events and graphs (not the workspace). */
 void ffp_batch_destroy(ffp_batch *B);
 
+/* ------------------------------------------------------------------------
+ * Learned filter.  Sec. I: a preconditioner with B t = A t removes the error
+ * component along t, and the components hardest to damp lie along the
+ * eigenvectors of the smallest eigenvalues of B^{-1}A, so t should
+ * approximate those; the paper itself uses t = 1.  The library can learn t:
+ * a 3-D convolutional network maps log10(kappa) to t, trained on targets
+ * built from Lanczos Ritz vectors of B_rowsum^{-1} A.  The network is not in
+ * the paper.  Its t is passed to ffp_setup as FFP_FILTER_USER; PCG still
+ * solves to the same tolerance, so correctness never depends on it.
+ *
+ * Network: x0 = log10(kappa) / 3; four 3x3x3 convolutions with zero padding,
+ * channels 1 -> 16 -> 16 -> 16 -> 1, ReLU after the first three; output s,
+ * t = exp(s).  Parameters: FP32 [FFP_NET_PARAMS], per layer the weights
+ * w[out][in][dz][dy][dx] then the biases (offsets 0, 432 | 448, 7360 |
+ * 7376, 14288 | 14304, 14736).  The convolutions use BF16 copies of the
+ * weights (`wbf16`, the BF16 bit patterns, kept in step by ffp_net_cast or
+ * ffp_net_adam) and FP32 arithmetic.  Batches hold `batch` instances of one
+ * grid, instance-major: kappa [batch][N].
+ * ------------------------------------------------------------------------ */
+#define FFP_NET_PARAMS 14737
+
+/* Workspace bytes for a forward pass (train = 0) or a gradient (train = 1);
+ * 0 for a bad grid or batch. */
+size_t ffp_net_workspace_bytes(const ffp_grid *grid, int batch, int train);
+
+/* He-normal weights (std sqrt(2 / (27 * in))) from a host generator seeded by
+ * `seed`, zero biases, and their BF16 copy.  Synchronises `stream`. */
+int ffp_net_init(unsigned long long seed, float *params, unsigned short *wbf16, void *stream);
+
+/* wbf16 = BF16(params) (round to nearest even). */
+int ffp_net_cast(const float *params, unsigned short *wbf16, void *stream);
+
+/* t = exp(clamp(s, -30, 30)) [batch][N] FP64 device, s the network's output. */
+int ffp_net_forward(const ffp_grid *grid, int batch, const double *kappa, const float *params,
+                    const unsigned short *wbf16, void *workspace, size_t ws_bytes, double *t,
+                    void *stream);
+
+/* Gradient of L = mean over cells of (s - s_target)^2 w.r.t. every parameter
+ * (through the BF16 weights the forward pass used), into grad FP32
+ * [FFP_NET_PARAMS] (device); loss: host pointer or NULL (then the call does
+ * not synchronise).  s_target: FP32 [batch][N] device. */
+int ffp_net_grad(const ffp_grid *grid, int batch, const double *kappa, const float *s_target,
+                 const float *params, const unsigned short *wbf16, void *workspace,
+                 size_t ws_bytes, float *grad, double *loss, void *stream);
+
+/* One Adam step (b1 0.9, b2 0.999, eps 1e-8; step = 1, 2, ... for the bias
+ * correction) on params with moments m, v (FP32 device, start at zero), and
+ * the new BF16 copy. */
+int ffp_net_adam(float *params, unsigned short *wbf16, float *m, float *v, const float *grad,
+                 int step, double lr, void *stream);
+
+/* Lanczos on B_NTD^{-1} A (self-adjoint in the A-inner product) with full
+ * re-orthogonalisation, from start vector v0 (device FP64 [N]), at most m
+ * steps (m <= 64): Ritz values theta (host [m], ascending; *steps of them are
+ * set) and the A-normalised Ritz vectors of the nvec <= 8 smallest, Y (device
+ * FP64 [nvec][N]).  For a handle built with FFP_PRECOND_COMBO the nested
+ * sweeps B_NTD^{-1} alone are used.  scratch: device, 256-byte aligned, >=
+ * ffp_lanczos_scratch_bytes(grid, m).  Synchronises `stream` at every step.
+ * FFP_ERR_BREAKDOWN if v0 has no positive A-norm. */
+size_t ffp_lanczos_scratch_bytes(const ffp_grid *grid, int m);
+int ffp_lanczos_ritz(ffp_handle *h, const double *v0, int m, int nvec, void *scratch,
+                     size_t scratch_bytes, double *theta, double *Y, int *steps, void *stream);
+
+/* Training target of the learned filter from nvec Ritz pairs (theta host
+ * [nvec] > 0, Y device [nvec][N]): t* = sqrt(sum_k (theta_0 / theta_k)
+ * (y_k / max|y_k|)^2), scaled to max 1 and floored at floor_ (0 < floor_ <=
+ * 1), into t (device FP64 [N]); s = log t* minus its mean into s (device FP32
+ * [N]).  scratch as for ffp_lanczos_ritz with m = 1 or more.  Synchronises
+ * `stream`. */
+int ffp_filter_target(const ffp_grid *grid, int nvec, const double *theta, const double *Y,
+                      double floor_, double *t, float *s, void *scratch, size_t scratch_bytes,
+                      void *stream);
+
 /* Static text for a status code. */
 const char *ffp_strerror(int status);
 

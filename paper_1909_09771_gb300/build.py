@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libffp.so")
 SOURCES = ["ffp_api.cu", "ffp_ops.cu", "ffp_dispatch.cu", "ffp_setup_a.cu", "ffp_setup_b.cu",
            "ffp_setup_c.cu", "ffp_setup_d.cu", "ffp_setup_e.cu", "ffp_apply_f64.cu", "ffp_apply_f32.cu",
-           "ffp_apply_bf16.cu", "ffp_ilu.cu", "ffp_batch.cu"]
+           "ffp_apply_bf16.cu", "ffp_ilu.cu", "ffp_batch.cu", "ffp_net.cu", "ffp_lanczos.cu"]
 HEADERS = ["ffp_internal.cuh", "ffp_plane.cuh", "ffp_kernels.h", "ffp_setup.cuh", "ffp_apply.cuh",
            "ffp_vecops.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -21,6 +21,9 @@ struct ffp_handle {
     cudaEvent_t ev[4];  // preconditioner timing: start, B_NTD sweeps start and end, end
 };
 
+const KernelCtx *ffp::handle_ctx(const ffp_handle *h) { return h ? &h->c : nullptr; }
+int ffp::handle_device(const ffp_handle *h) { return h ? h->device : -1; }
+
 size_t ffp::prec_bytes(int prec) {
     switch (prec) {
         case FFP_FP64: return 8;

@@ -21,6 +21,9 @@ struct KernelCtx {
 // ffp_api.cu: bytes per stored factor value, and the workspace layout (base may
 // be null to size it; S_force > 0 forces the line slot count)
 size_t prec_bytes(int prec);
+// ffp_api.cu: the kernel context and device of a handle
+const KernelCtx *handle_ctx(const ffp_handle *h);
+int handle_device(const ffp_handle *h);
 size_t carve_workspace(const ffp_grid *g, int prec, int S_force, char *base, Ws *ws);
 
 // ffp_ops.cu

@@ -62,6 +62,7 @@ class BatchConfig(ctypes.Structure):
 
 
 FFP_BATCH_MAX_PAIRS = 65535
+FFP_NET_PARAMS = 14737
 
 
 class FFPError(RuntimeError):
@@ -113,9 +114,25 @@ def load():
     lib.ffp_batch_solve.argtypes = [vp, P(vp), P(vp), ctypes.c_double, ctypes.c_int, P(Stats), vp]
     lib.ffp_batch_destroy.argtypes = [vp]
     lib.ffp_batch_destroy.restype = None
+    lib.ffp_net_workspace_bytes.argtypes = [P(Grid), ctypes.c_int, ctypes.c_int]
+    lib.ffp_net_workspace_bytes.restype = ctypes.c_size_t
+    lib.ffp_net_init.argtypes = [ctypes.c_ulonglong, vp, vp, vp]
+    lib.ffp_net_cast.argtypes = [vp, vp, vp]
+    lib.ffp_net_forward.argtypes = [P(Grid), ctypes.c_int, vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
+    lib.ffp_net_grad.argtypes = [P(Grid), ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_size_t, vp,
+                                 P(ctypes.c_double), vp]
+    lib.ffp_net_adam.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]
+    lib.ffp_lanczos_scratch_bytes.argtypes = [P(Grid), ctypes.c_int]
+    lib.ffp_lanczos_scratch_bytes.restype = ctypes.c_size_t
+    lib.ffp_lanczos_ritz.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t,
+                                     P(ctypes.c_double), vp, P(ctypes.c_int), vp]
+    lib.ffp_filter_target.argtypes = [P(Grid), ctypes.c_int, P(ctypes.c_double), vp,
+                                      ctypes.c_double, vp, vp, vp, ctypes.c_size_t, vp]
     for f in (lib.ffp_setup, lib.ffp_spmv, lib.ffp_apply, lib.ffp_pcg_solve, lib.ffp_export,
               lib.ffp_apply_noalloc, lib.ffp_batch_setup, lib.ffp_batch_tune, lib.ffp_batch_get_config,
-              lib.ffp_batch_set_config, lib.ffp_batch_info, lib.ffp_batch_solve):
+              lib.ffp_batch_set_config, lib.ffp_batch_info, lib.ffp_batch_solve, lib.ffp_net_init,
+              lib.ffp_net_cast, lib.ffp_net_forward, lib.ffp_net_grad, lib.ffp_net_adam,
+              lib.ffp_lanczos_ritz, lib.ffp_filter_target):
         f.restype = ctypes.c_int
     _lib = lib
     return lib

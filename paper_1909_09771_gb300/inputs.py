@@ -142,3 +142,15 @@ def random_small(grid, seed, contrast_exp=3, bc=BC_Z_DIRICHLET, per_cell=False):
         kappa = kappa_blocks(grid, 2, None, emin=-contrast_exp, emax=contrast_exp, rng=rng)
     b = rng.standard_normal(n)
     return dict(name=f"rand{grid}", grid=tuple(grid), kappa=kappa, bc=tuple(bc), b=b)
+
+
+def lanczos_start(n, seed):
+    """Start vector of a Lanczos run: N(0,1) per cell from default_rng(seed)."""
+    return np.random.default_rng(seed).standard_normal(int(n))
+
+
+def workload_learned_train(count=2000, n=64, seed0=10_000, exponent=2.0):
+    """Training instances of the learned filter: instance i is the n^3 GRF of
+    seed seed0 + i with kappa = 10^(exponent g) (contrast 10^(2 exponent))."""
+    for i in range(count):
+        yield workload_grf(seed=seed0 + i, n=n, exponent=exponent)

@@ -1,0 +1,173 @@
+"""Learned filter vector t for the nested filtering preconditioner.
+
+Sec. I of the paper: with B t = A t the error component along t is removed,
+and the slowest components lie along the eigenvectors of the smallest
+eigenvalues of B^{-1}A, so t should approximate them.  This module trains the
+library's convolutional network (include/ffp.h, "Learned filter") to predict
+such a t from log10(kappa):
+  1. targets: for each training instance, Lanczos Ritz vectors of
+     B_rowsum^{-1} A (ffp_lanczos_ritz) -> t*, s* = log t* - mean
+     (ffp_filter_target);
+  2. training: minibatches of (kappa, s*) -> ffp_net_grad -> ffp_net_adam;
+  3. use: ffp_net_forward gives t, passed to ffp_setup as FFP_FILTER_USER.
+Host orchestration only: every arithmetic step is a call into libffp.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import ffp
+from . import inputs as I
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class FilterNet:
+    """Network parameters (FP32 master copy, BF16 copy, Adam moments) on one device."""
+
+    def __init__(self, seed=0, device="cuda", stream=None):
+        lib = ffp.load()
+        self.device = torch.device(device)
+        P = ffp.FFP_NET_PARAMS
+        self.params = torch.zeros(P, dtype=torch.float32, device=self.device)
+        self.wbf16 = torch.zeros(P, dtype=torch.int16, device=self.device)
+        self.m = torch.zeros(P, dtype=torch.float32, device=self.device)
+        self.v = torch.zeros(P, dtype=torch.float32, device=self.device)
+        self.step = 0
+        st = lib.ffp_net_init(ctypes.c_ulonglong(seed), _p(self.params), _p(self.wbf16),
+                              ffp._stream(stream))
+        if st != ffp.FFP_OK:
+            raise ffp.FFPError(st, "ffp_net_init")
+        self._ws = {}
+
+    def load(self, params, stream=None):
+        """Set the FP32 parameters (and their BF16 copy) from an array."""
+        self.params.copy_(torch.as_tensor(np.asarray(params, dtype=np.float32)))
+        st = ffp.load().ffp_net_cast(_p(self.params), _p(self.wbf16), ffp._stream(stream))
+        if st != ffp.FFP_OK:
+            raise ffp.FFPError(st, "ffp_net_cast")
+
+    def _workspace(self, grid, batch, train):
+        key = (tuple(grid), batch, train)
+        if key not in self._ws:
+            g = ffp._grid(grid, (1.0, 1.0, 1.0))
+            nb = ffp.load().ffp_net_workspace_bytes(ctypes.byref(g), batch, train)
+            if nb == 0:
+                raise ffp.FFPError(ffp.FFP_ERR_ARG, "ffp_net_workspace_bytes")
+            self._ws = {key: torch.empty(nb, dtype=torch.uint8, device=self.device)}
+        return self._ws[key]
+
+    def forward(self, grid, kappa, batch=1, t=None, stream=None):
+        """t = exp(s) for `batch` instances (kappa FP64 [batch * N] device)."""
+        n = int(np.prod(grid))
+        ws = self._workspace(grid, batch, 0)
+        t = torch.empty(batch * n, dtype=torch.float64, device=self.device) if t is None else t
+        g = ffp._grid(grid, (1.0, 1.0, 1.0))
+        st = ffp.load().ffp_net_forward(ctypes.byref(g), batch, _p(kappa), _p(self.params),
+                                        _p(self.wbf16), _p(ws), ctypes.c_size_t(ws.numel()), _p(t),
+                                        ffp._stream(stream))
+        if st != ffp.FFP_OK:
+            raise ffp.FFPError(st, "ffp_net_forward")
+        return t
+
+    def grad(self, grid, kappa, s_target, batch=1, grad=None, stream=None, want_loss=True):
+        ws = self._workspace(grid, batch, 1)
+        grad = torch.empty(ffp.FFP_NET_PARAMS, dtype=torch.float32, device=self.device) \
+            if grad is None else grad
+        g = ffp._grid(grid, (1.0, 1.0, 1.0))
+        loss = ctypes.c_double(0.0)
+        st = ffp.load().ffp_net_grad(ctypes.byref(g), batch, _p(kappa), _p(s_target),
+                                     _p(self.params), _p(self.wbf16), _p(ws),
+                                     ctypes.c_size_t(ws.numel()), _p(grad),
+                                     ctypes.byref(loss) if want_loss else None, ffp._stream(stream))
+        if st != ffp.FFP_OK:
+            raise ffp.FFPError(st, "ffp_net_grad")
+        return grad, (loss.value if want_loss else None)
+
+    def adam(self, grad, lr=1e-3, stream=None):
+        self.step += 1
+        st = ffp.load().ffp_net_adam(_p(self.params), _p(self.wbf16), _p(self.m), _p(self.v),
+                                     _p(grad), self.step, float(lr), ffp._stream(stream))
+        if st != ffp.FFP_OK:
+            raise ffp.FFPError(st, "ffp_net_adam")
+
+
+def lanczos_ritz(P, m=40, nvec=8, seed=0, stream=None):
+    """Ritz values (numpy, ascending) and the nvec smallest A-normalised Ritz
+    vectors (device FP64 [nvec][N]) of B_NTD^{-1}A for Preconditioner P."""
+    lib = ffp.load()
+    n = P.n
+    g = ffp._grid(P.grid, (1.0, 1.0, 1.0))
+    nb = lib.ffp_lanczos_scratch_bytes(ctypes.byref(g), m)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=P.workspace.device)
+    v0 = torch.as_tensor(I.lanczos_start(n, seed), device=P.workspace.device)
+    Y = torch.empty(max(nvec, 1) * n, dtype=torch.float64, device=P.workspace.device)
+    theta = (ctypes.c_double * m)()
+    steps = ctypes.c_int(0)
+    st = lib.ffp_lanczos_ritz(P._h, _p(v0), m, nvec, _p(scratch), ctypes.c_size_t(nb), theta, _p(Y),
+                              ctypes.byref(steps), ffp._stream(stream))
+    if st != ffp.FFP_OK:
+        raise ffp.FFPError(st, "ffp_lanczos_ritz")
+    return np.array(theta[:steps.value]), Y.view(nvec, n) if nvec > 0 else None, scratch
+
+
+def filter_target(grid, theta, Y, nvec=8, floor=1e-2, scratch=None, stream=None):
+    """(t* FP64, s* FP32) device vectors from the Ritz pairs."""
+    lib = ffp.load()
+    n = int(np.prod(grid))
+    g = ffp._grid(grid, (1.0, 1.0, 1.0))
+    nb = lib.ffp_lanczos_scratch_bytes(ctypes.byref(g), 1)
+    if scratch is None or scratch.numel() < nb:
+        scratch = torch.empty(nb, dtype=torch.uint8, device=Y.device)
+    t = torch.empty(n, dtype=torch.float64, device=Y.device)
+    s = torch.empty(n, dtype=torch.float32, device=Y.device)
+    th = (ctypes.c_double * nvec)(*[float(v) for v in theta[:nvec]])
+    st = lib.ffp_filter_target(ctypes.byref(g), nvec, th, _p(Y), float(floor), _p(t), _p(s),
+                               _p(scratch), ctypes.c_size_t(scratch.numel()), ffp._stream(stream))
+    if st != ffp.FFP_OK:
+        raise ffp.FFPError(st, "ffp_filter_target")
+    return t, s
+
+
+def make_targets(instances, m=40, nvec=8, floor=1e-2, precision="fp32", device="cuda"):
+    """Per instance: kappa (device FP64) and the target s* (device FP32)."""
+    kappas, targets = [], []
+    for k, w in enumerate(instances):
+        kap = torch.as_tensor(w["kappa"], device=device)
+        P = ffp.Preconditioner(w["grid"], kap, w["bc"], precision, precond="ntd")
+        theta, Y, scratch = lanczos_ritz(P, m=m, nvec=nvec, seed=k)
+        _, s = filter_target(w["grid"], theta, Y, nvec=nvec, floor=floor, scratch=scratch)
+        P.close()
+        kappas.append(kap)
+        targets.append(s)
+    return kappas, targets
+
+
+def train(net, grid, kappas, targets, epochs=4, batch=8, lr=1e-3, seed=0, log=None):
+    """Adam on minibatches of `batch` instances; returns the mean loss per epoch."""
+    n = int(np.prod(grid))
+    dev = net.device
+    kb = torch.empty(batch * n, dtype=torch.float64, device=dev)
+    sb = torch.empty(batch * n, dtype=torch.float32, device=dev)
+    g = torch.empty(ffp.FFP_NET_PARAMS, dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        order = rng.permutation(len(kappas))
+        losses = []
+        for b0 in range(0, len(order) - batch + 1, batch):
+            for j, i in enumerate(order[b0:b0 + batch]):
+                kb[j * n:(j + 1) * n].copy_(kappas[i])
+                sb[j * n:(j + 1) * n].copy_(targets[i])
+            _, loss = net.grad(grid, kb, sb, batch=batch, grad=g)
+            net.adam(g, lr=lr)
+            losses.append(loss)
+        hist.append(float(np.mean(losses)))
+        if log:
+            log(f"epoch {ep}: loss {hist[-1]:.4f}")
+    return hist

@@ -1,0 +1,191 @@
+"""Learned filter on the GPU (include/ffp.h, "Learned filter") against the FP64
+oracle of oracle/convnet.py.
+
+Tolerances: the GPU network computes in FP32 with BF16 weights; the oracle runs
+in FP64 on the same BF16-rounded weights and FP32 biases, so the only
+difference is FP32 rounding: about 1e-7 per operation over 432-term sums and,
+for the weight gradient, sums over every cell of a batch.
+  forward s            1e-5 of max |s|
+  gradient, per layer  1e-4 relative 2-norm (reductions over ~10^4-10^5 cells)
+  Adam step            1e-6 relative (a few FP32 operations per parameter)
+  Lanczos (FP64)       Ritz values 1e-8 relative; Ritz vectors A-cosine >= 1 - 1e-6
+                       (same algorithm; the GPU's factors differ from the oracle's
+                       at 1e-10, its reductions round in another order)
+  target               1e-12 relative on the same Ritz pairs
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import convnet as C
+from oracle import oracle as o
+from paper_1909_09771_gb300 import build as B
+from paper_1909_09771_gb300 import ffp
+from paper_1909_09771_gb300 import inputs as I
+from paper_1909_09771_gb300 import learned as L
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    ffp.load()
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+OFF = [(0, 432, 1, 16), (448, 7360, 16, 16), (7376, 14288, 16, 16), (14304, 14736, 16, 1)]
+
+
+def oracle_params(net):
+    """The network's weights as the GPU uses them: BF16-rounded weights, FP32 biases."""
+    p = host(net.params).astype(np.float64)
+    out = []
+    for w0, b0, cin, cout in OFF:
+        w = C.bf16_round(p[w0:w0 + cout * cin * 27]).reshape(cout, cin, 3, 3, 3)
+        out.append((w, p[b0:b0 + cout].copy()))
+    return out
+
+
+def flat_grads(grads):
+    g = np.zeros(ffp.FFP_NET_PARAMS)
+    for (w0, b0, cin, cout), (gw, gb) in zip(OFF, grads):
+        g[w0:w0 + gw.size] = gw.ravel()
+        g[b0:b0 + cout] = gb
+    return g
+
+
+def net_with_biases(seed):
+    net = L.FilterNet(seed=seed)
+    p = host(net.params).copy()
+    rng = np.random.default_rng(seed + 100)
+    for _, b0, _, cout in OFF:
+        p[b0:b0 + cout] = rng.uniform(-0.2, 0.2, cout)
+    net.load(p)
+    return net
+
+
+# several tiles (32 x 4 x 2) with ragged edges in every direction, and a tiny grid
+GRIDS = [(37, 9, 5), (5, 3, 2), (64, 4, 2)]
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_forward_matches_oracle(grid):
+    net = net_with_biases(1)
+    n = int(np.prod(grid))
+    batch = 2
+    kap = np.concatenate([I.random_small(grid, 40 + k, contrast_exp=3, per_cell=True)["kappa"]
+                          for k in range(batch)])
+    t = host(net.forward(grid, dev(kap), batch=batch))
+    par = oracle_params(net)
+    for k in range(batch):
+        s_ref, _ = C.forward(par, C.features(kap[k * n:(k + 1) * n], grid))
+        s = np.log(t[k * n:(k + 1) * n]).reshape(s_ref.shape)
+        assert np.max(np.abs(s - s_ref)) <= 1e-5 * max(1.0, np.max(np.abs(s_ref)))
+
+
+@pytest.mark.parametrize("grid", GRIDS[:2])
+def test_gradient_matches_oracle(grid):
+    net = net_with_biases(2)
+    n = int(np.prod(grid))
+    batch = 2
+    rng = np.random.default_rng(7)
+    kap = np.concatenate([I.random_small(grid, 50 + k, contrast_exp=3, per_cell=True)["kappa"]
+                          for k in range(batch)])
+    st = rng.standard_normal(batch * n).astype(np.float32)
+    g, loss = net.grad(grid, dev(kap), torch.as_tensor(st, device="cuda"), batch=batch)
+    g = host(g).astype(np.float64)
+    par = oracle_params(net)
+    # the oracle's loss is a mean over one instance; over the batch it is the mean of the means
+    total = [np.zeros_like(w) for w, _ in par], [np.zeros_like(b) for _, b in par]
+    lsum = 0.0
+    for k in range(batch):
+        x0 = C.features(kap[k * n:(k + 1) * n], grid)
+        s, acts = C.forward(par, x0)
+        lk, gs = C.loss_and_grad(s, st[k * n:(k + 1) * n].astype(np.float64).reshape(s.shape))
+        grads = C.backward(par, acts, gs / batch)
+        lsum += lk / batch
+        for i, (gw, gb) in enumerate(grads):
+            total[0][i] += gw
+            total[1][i] += gb
+    ref = flat_grads(list(zip(total[0], total[1])))
+    assert abs(loss - lsum) <= 1e-6 * lsum
+    for w0, b0, cin, cout in OFF:
+        for lo, hi in ((w0, w0 + cout * cin * 27), (b0, b0 + cout)):
+            err = np.linalg.norm(g[lo:hi] - ref[lo:hi]) / max(np.linalg.norm(ref[lo:hi]), 1e-30)
+            assert err <= 1e-4, (w0, lo, err)
+
+
+def test_adam_matches_oracle():
+    net = net_with_biases(3)
+    rng = np.random.default_rng(8)
+    p0 = host(net.params).astype(np.float64)
+    gsteps = [rng.standard_normal(ffp.FFP_NET_PARAMS).astype(np.float32) for _ in range(3)]
+    state = {}
+    par = [(p0.reshape(1, 1, 1, 1, -1).copy(), np.zeros(1))]
+    for g in gsteps:
+        net.adam(torch.as_tensor(g, device="cuda"), lr=1e-3)
+        par = C.adam_step(par, [(g.astype(np.float64).reshape(1, 1, 1, 1, -1), np.zeros(1))], state,
+                          lr=1e-3)
+    p = host(net.params).astype(np.float64)
+    ref = par[0][0].ravel()
+    assert np.max(np.abs(p - ref)) <= 1e-6 * max(1.0, np.max(np.abs(ref)))
+    # the BF16 copy follows the FP32 parameters
+    wb = host(net.wbf16).astype(np.uint16).astype(np.uint32) << 16
+    assert np.array_equal(wb.view(np.float32).astype(np.float64), C.bf16_round(p.astype(np.float32)))
+
+
+@pytest.mark.parametrize("grid", [(10, 8, 6), (33, 5, 4)])
+def test_lanczos_matches_oracle(grid):
+    w = I.random_small(grid, 60, contrast_exp=2)
+    n = int(np.prod(grid))
+    P = ffp.Preconditioner(grid, dev(w["kappa"]), w["bc"], "fp64", precond="ntd")
+    m = 24
+    theta, Y, _ = L.lanczos_ritz(P, m=m, nvec=4, seed=5)
+    bands = o.assemble(grid, w["kappa"], w["bc"])
+    f = o.setup(grid, bands)
+    th_ref, Y_ref, _, _ = C.lanczos_ritz(lambda x: o.spmv(grid, bands, x), lambda r: o.apply(f, r),
+                                         I.lanczos_start(n, 5), m)
+    assert len(theta) == len(th_ref)
+    assert np.max(np.abs(theta[:4] - th_ref[:4]) / th_ref[:4]) <= 1e-8
+    Yg = host(Y)
+    for k in range(4):
+        y, r = Yg[k], Y_ref[:, k]
+        Ay = o.spmv(grid, bands, y)
+        cos = abs(r @ Ay) / np.sqrt((y @ Ay) * (r @ o.spmv(grid, bands, r)))
+        assert cos >= 1 - 1e-6, (k, cos)
+        assert abs(y @ Ay - 1.0) <= 1e-8   # A-normalised
+
+
+def test_filter_target_matches_oracle():
+    grid = (12, 9, 7)
+    w = I.random_small(grid, 61, contrast_exp=3)
+    P = ffp.Preconditioner(grid, dev(w["kappa"]), w["bc"], "fp64", precond="ntd")
+    theta, Y, scratch = L.lanczos_ritz(P, m=30, nvec=8, seed=6)
+    t, s = L.filter_target(grid, theta, Y, nvec=8, floor=0.02, scratch=scratch)
+    t_ref, s_ref = C.filter_target(theta, host(Y).T, nvec=8, floor=0.02)
+    assert np.max(np.abs(host(t) - t_ref)) <= 1e-12
+    assert np.max(np.abs(host(s).astype(np.float64) - s_ref)) <= 1e-6 * max(1.0, np.abs(s_ref).max())
+    # the target is a usable filter: setup accepts it and PCG converges with it
+    Pt = ffp.Preconditioner(grid, dev(w["kappa"]), w["bc"], "fp64", t=t, precond="combo")
+    _, st = Pt.solve(dev(w["b"]), rtol=1e-8, maxit=300)
+    assert st["status"] == 0 and st["rel_res_true"] < 1e-8
+
+
+def test_training_reduces_loss():
+    grid = (16, 16, 16)
+    insts = [I.workload_grf(seed=900 + k, n=16, exponent=2.0) for k in range(8)]
+    kappas, targets = L.make_targets(insts, m=20, nvec=8)
+    net = L.FilterNet(seed=4)
+    hist = L.train(net, grid, kappas, targets, epochs=6, batch=4, lr=3e-3)
+    assert all(np.isfinite(hist))
+    assert hist[-1] < hist[0]
