@@ -175,9 +175,17 @@ def run_ours(args):
     wsb = ffp.workspace_bytes(grid, args.precision)
     work = torch.empty(wsb, dtype=torch.uint8, device=dev)
 
+    net = None
+    if args.filter == "learned":
+        from paper_1909_09771_gb300 import learned as LF
+        net = LF.load_weights(args.weights, device=dev)
+        t_buf = torch.empty(n, dtype=torch.float64, device=dev)
+
     def step(kap, rhs, xout):
+        # learned filter: the network's inference on this kappa is part of the step
+        t = net.forward(grid, kap, batch=1, t=t_buf) if net is not None else None
         P = ffp.Preconditioner(grid, kap, bc, args.precision, precond=args.precond,
-                               workspace=work)
+                               workspace=work, t=t)
         xout.zero_()
         _, st = P.solve(rhs, x=xout, rtol=RTOL, maxit=MAXIT, check=False)
         P.close()
@@ -246,7 +254,8 @@ def run_ours(args):
             "precond": {"combo": "B_c = NTD + ILU(0) (Sec. III Eq. (com))",
                         "ntd": "B_NTD (Sec. II)"}[args.precond],
             "factors": args.precision,
-            "filter": "rowsum",
+            "filter": args.filter if args.filter == "rowsum" else
+            "learned (conv net on log10 kappa, weights " + os.path.basename(args.weights) + ")",
             "rtol": RTOL,
             "iters": st["iters"],
             "rel_res_true": st["rel_res_true"],
@@ -271,7 +280,8 @@ def run_ours(args):
         "e2e": {"value": e2e_ms / 1e3 / ws, "unit": "s",
                 "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(sum(s["launches"] for s in stats))
-        + args.steps * ffp.setup_launches(grid, args.precond),
+        + args.steps * (ffp.setup_launches(grid, args.precond, user_t=net is not None)
+                        + (6 if net is not None else 0)),
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -522,6 +532,9 @@ def main():
     ap.add_argument("--workload", default="grf350")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--precond", default="combo", choices=["combo", "ntd"])
+    ap.add_argument("--filter", default="rowsum", choices=["rowsum", "learned"])
+    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1909_09771_gb300",
+                                                        "learned_filter_weights.txt"))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-sample-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -116,7 +116,10 @@ def lanczos_ritz(P, m=40, nvec=8, seed=0, stream=None):
     return np.array(theta[:steps.value]), Y.view(nvec, n) if nvec > 0 else None, scratch
 
 
-def filter_target(grid, theta, Y, nvec=8, floor=1e-2, scratch=None, stream=None):
+FLOOR = 0.1   # target floor (relative to max t*): the value that helps B_c PCG on 64^3 GRFs
+
+
+def filter_target(grid, theta, Y, nvec=8, floor=FLOOR, scratch=None, stream=None):
     """(t* FP64, s* FP32) device vectors from the Ritz pairs."""
     lib = ffp.load()
     n = int(np.prod(grid))
@@ -134,10 +137,16 @@ def filter_target(grid, theta, Y, nvec=8, floor=1e-2, scratch=None, stream=None)
     return t, s
 
 
-def make_targets(instances, m=40, nvec=8, floor=1e-2, precision="fp32", device="cuda"):
-    """Per instance: kappa (device FP64) and the target s* (device FP32)."""
+def make_targets(instances, m=40, nvec=8, floor=FLOOR, precision="fp32", device="cuda",
+                 max_seconds=None):
+    """Per instance: kappa (device FP64) and the target s* (device FP32); stops
+    early once max_seconds have passed."""
+    import time
+    t0 = time.time()
     kappas, targets = [], []
     for k, w in enumerate(instances):
+        if max_seconds is not None and time.time() - t0 > max_seconds:
+            break
         kap = torch.as_tensor(w["kappa"], device=device)
         P = ffp.Preconditioner(w["grid"], kap, w["bc"], precision, precond="ntd")
         theta, Y, scratch = lanczos_ritz(P, m=m, nvec=nvec, seed=k)
@@ -171,3 +180,98 @@ def train(net, grid, kappas, targets, epochs=4, batch=8, lr=1e-3, seed=0, log=No
         if log:
             log(f"epoch {ep}: loss {hist[-1]:.4f}")
     return hist
+
+
+WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__file__), "learned_filter_weights.txt")
+
+
+def save_weights(net, path):
+    np.savetxt(path, net.params.detach().cpu().numpy().astype(np.float64), fmt="%.9e")
+
+
+def load_weights(path=WEIGHTS, seed=0, device="cuda"):
+    net = FilterNet(seed=seed, device=device)
+    net.load(np.loadtxt(path))
+    return net
+
+
+def predict_filter(net, w, device="cuda"):
+    """t for one instance (dict with grid and kappa), device FP64."""
+    kap = torch.as_tensor(w["kappa"], device=device)
+    return net.forward(w["grid"], kap, batch=1)
+
+
+def _main(argv=None):
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(description="train / evaluate the learned filter network")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    tr = sub.add_parser("train")
+    tr.add_argument("--count", type=int, default=2000)
+    tr.add_argument("--n", type=int, default=64)
+    tr.add_argument("--epochs", type=int, default=6)
+    tr.add_argument("--batch", type=int, default=8)
+    tr.add_argument("--lr", type=float, default=2e-3)
+    tr.add_argument("--out", default=WEIGHTS)
+    tr.add_argument("--log", default=None)
+    tr.add_argument("--max-target-seconds", type=float, default=None)
+    ev = sub.add_parser("eval")
+    ev.add_argument("--weights", default=WEIGHTS)
+    ev.add_argument("--n", type=int, default=64)
+    ev.add_argument("--exponent", type=float, default=2.0)
+    ev.add_argument("--seeds", default="0,1")
+    ev.add_argument("--precision", default="fp32")
+    ev.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    ffp.load()
+    dev = torch.device("cuda")
+    if a.cmd == "train":
+        t0 = time.time()
+        insts = I.workload_learned_train(count=a.count, n=a.n)
+        kappas, targets = make_targets(insts, max_seconds=a.max_target_seconds)
+        t_targets = time.time() - t0
+        print(f"targets: {len(kappas)} instances in {t_targets:.1f} s", flush=True)
+        net = FilterNet(seed=0)
+        t0 = time.time()
+        hist = train(net, (a.n,) * 3, kappas, targets, epochs=a.epochs, batch=a.batch, lr=a.lr,
+                     log=print)
+        t_train = time.time() - t0
+        save_weights(net, a.out)
+        rep = {"count": len(kappas), "requested": a.count, "n": a.n, "epochs": a.epochs,
+               "batch": a.batch, "lr": a.lr,
+               "targets_s": t_targets, "train_s": t_train, "loss": hist}
+        print(json.dumps(rep))
+        if a.log:
+            with open(a.log, "w") as fh:
+                json.dump(rep, fh)
+    else:
+        net = load_weights(a.weights)
+        res = []
+        for sd in [int(v) for v in a.seeds.split(",")]:
+            w = I.workload_grf(seed=sd, n=a.n, exponent=a.exponent)
+            kap = torch.as_tensor(w["kappa"], device=dev)
+            b = torch.as_tensor(w["b"], device=dev)
+            row = {"seed": sd}
+            torch.cuda.synchronize()
+            t0 = time.time()
+            t = predict_filter(net, w)
+            torch.cuda.synchronize()
+            row["infer_s"] = time.time() - t0
+            for name, tt in (("rowsum", None), ("learned", t)):
+                t0 = time.time()
+                P = ffp.Preconditioner(w["grid"], kap, w["bc"], a.precision, t=tt, precond="combo")
+                x, st = P.solve(b, rtol=1e-8, maxit=1000, check=False)
+                torch.cuda.synchronize()
+                row[name] = {"iters": st["iters"], "status": st["status"],
+                             "rel_res_true": st["rel_res_true"], "s": time.time() - t0}
+                P.close()
+            res.append(row)
+            print(json.dumps(row), flush=True)
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(res, fh)
+
+
+if __name__ == "__main__":
+    _main()

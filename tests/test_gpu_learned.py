@@ -189,3 +189,30 @@ def test_training_reduces_loss():
     hist = L.train(net, grid, kappas, targets, epochs=6, batch=4, lr=3e-3)
     assert all(np.isfinite(hist))
     assert hist[-1] < hist[0]
+
+
+def test_trained_filter_gain_over_rowsum():
+    """The committed network (trained by `python -m paper_1909_09771_gb300.learned train`
+    on 2000 64^3 GRF instances, seeds 10000-11999) against the rowsum filter on held-out
+    instances: B_c flexible CG with FP32 factors to 1e-8.  The learned filter must never
+    break the solve (PCG still runs to the same tolerance) and must not cost more than two
+    iterations; its measured gain is reported."""
+    import os
+    if not os.path.exists(L.WEIGHTS):
+        pytest.skip("no trained weights")
+    net = L.load_weights()
+    gains = []
+    for seed in (0, 1):
+        w = I.workload_grf(seed=seed, n=64, exponent=2.0)
+        kap, b = dev(w["kappa"]), dev(w["b"])
+        t = L.predict_filter(net, w)
+        assert torch.all(t > 0) and torch.all(torch.isfinite(t))
+        its = {}
+        for name, tt in (("rowsum", None), ("learned", t)):
+            P = ffp.Preconditioner(w["grid"], kap, w["bc"], "fp32", t=tt, precond="combo")
+            _, st = P.solve(b, rtol=1e-8, maxit=500)
+            assert st["status"] == 0 and st["rel_res_true"] < 1e-8
+            its[name] = st["iters"]
+        gains.append(its["rowsum"] - its["learned"])
+        assert its["learned"] <= its["rowsum"] + 2, its
+    print(f"learned filter gain (iterations saved) on held-out 64^3: {gains}")
