@@ -78,6 +78,7 @@ size_t ffp::carve_workspace(const ffp_grid *g, int prec, int S_force, char *base
         for (int b = 0; b < 2; ++b) w.sW[h][b] = (double *)take(8 * nxy);
         for (int b = 0; b < 3; ++b) w.sC[h][b] = (double *)take(8 * nxy);
     }
+    w.ilu_ready = (int *)take(4 * (size_t)g->ny * g->nz);
     w.red = (double *)take(8 * (size_t)kRedSlots);
     // scalar block and flags are contiguous so one copy brings both back
     w.scal = (double *)take(8 * (size_t)kScal + 4 * 16);
@@ -98,7 +99,7 @@ long long ntd_launches(const KernelCtx &c) {
     const int mz = (c.nz - 1) / 2;
     return ((mz > 0 || c.nz - 1 - mz > 0) ? 3 : 1) + (c.prec != FFP_FP64 ? 2 : 0);
 }
-long long ilu_launches(const KernelCtx &c) { return 2LL * (c.ny + c.nz - 1); }
+long long ilu_launches(const KernelCtx &c) { return ilu_solve_launches(c); }
 
 // z = B^{-1} r for the handle's preconditioner (r and z distinct from c1, c2).
 // ev (optional): events recorded at the start, just before and just after the

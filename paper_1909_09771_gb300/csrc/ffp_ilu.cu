@@ -151,17 +151,19 @@ __device__ __forceinline__ bool ilu_pair(const IluArgs &A0, const IluArgs *table
     return !A.ctl || (*A.ctl & 1);
 }
 
-template <int S, typename F>
-__global__ void __launch_bounds__(256) ilu_fwd_kernel(IluArgs A0, const IluArgs *__restrict__ table, int s) {
+// Loads of t values other warps of the same launch may have written (dataflow
+// form): through L2, never a stale L1 line.
+template <bool COH>
+__device__ __forceinline__ double ld_t(const double *p) {
+    if constexpr (COH) return __ldcg(p);
+    else return *p;
+}
+
+// Forward sweep of line (y, z): t = L^{-1} r along x (Sec. III, ILU(0) of blkD(A)).
+template <int S, typename F, bool COH>
+__device__ __forceinline__ void ilu_fwd_line(const IluView<F> &A, const IluGeo &g, int y, int z,
+                                             int lane) {
     using R = typename Compute<F>::type;
-    IluArgs a0;
-    if (!ilu_pair(A0, table, a0)) return;
-    const IluView<F> A(a0);
-    const IluGeo g = ilu_geo(A.nx, A.ny, A.nz);
-    const int lane = threadIdx.x & 31;
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int y, z;
-    if (!diag_line(g, s, j, y, z)) return;
     const long long base = (long long)A.nx * y + g.nxy * z;
     int cnt = A.nx - lane * S;
     cnt = cnt < 0 ? 0 : (cnt > S ? S : cnt);
@@ -176,8 +178,8 @@ __global__ void __launch_bounds__(256) ilu_fwd_kernel(IluArgs A0, const IluArgs 
             const long long lo = (a < g.M) ? 0 : g.M;
             const R di = ldf<true, F, R>(A.dinv + a);
             R v = (R)__ldg(A.r + a);
-            if (y > 0 && a - A.nx >= lo) v -= ldf<true, F, R>(A.ly + a - A.nx) * (R)A.t[a - A.nx];
-            if (z > 0 && a - g.nxy >= lo) v -= ldf<true, F, R>(A.lz + a - g.nxy) * (R)A.t[a - g.nxy];
+            if (y > 0 && a - A.nx >= lo) v -= ldf<true, F, R>(A.ly + a - A.nx) * (R)ld_t<COH>(A.t + a - A.nx);
+            if (z > 0 && a - g.nxy >= lo) v -= ldf<true, F, R>(A.lz + a - g.nxy) * (R)ld_t<COH>(A.t + a - g.nxy);
             al[k] = (x > 0 && a - 1 >= lo) ? -di * ldf<true, F, R>(A.lx + a - 1) : R(0);
             be[k] = di * v;
         }
@@ -200,18 +202,12 @@ __global__ void __launch_bounds__(256) ilu_fwd_kernel(IluArgs A0, const IluArgs 
     }
 }
 
-// backward: z_a = t_a - dinv_a (lx_a z_{a+1} + ly_a z_{a+nx} + lz_a z_{a+nxy}), in place on t
-template <int S, typename F>
-__global__ void __launch_bounds__(256) ilu_bwd_kernel(IluArgs A0, const IluArgs *__restrict__ table, int s) {
+// Backward sweep of line (y, z): z_a = t_a - dinv_a (lx_a z_{a+1} + ly_a z_{a+nx} +
+// lz_a z_{a+nxy}), in place on t.
+template <int S, typename F, bool COH>
+__device__ __forceinline__ void ilu_bwd_line(const IluView<F> &A, const IluGeo &g, int y, int z,
+                                             int lane) {
     using R = typename Compute<F>::type;
-    IluArgs a0;
-    if (!ilu_pair(A0, table, a0)) return;
-    const IluView<F> A(a0);
-    const IluGeo g = ilu_geo(A.nx, A.ny, A.nz);
-    const int lane = threadIdx.x & 31;
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int y, z;
-    if (!diag_line(g, s, j, y, z)) return;
     const long long base = (long long)A.nx * y + g.nxy * z;
     int cnt = A.nx - lane * S;
     cnt = cnt < 0 ? 0 : (cnt > S ? S : cnt);
@@ -226,8 +222,8 @@ __global__ void __launch_bounds__(256) ilu_bwd_kernel(IluArgs A0, const IluArgs 
             const long long hi = (a < g.M) ? g.M : g.n;
             const R di = ldf<true, F, R>(A.dinv + a);
             R v = R(0);
-            if (y + 1 < A.ny && a + A.nx < hi) v += ldf<true, F, R>(A.ly + a) * (R)A.t[a + A.nx];
-            if (z + 1 < A.nz && a + g.nxy < hi) v += ldf<true, F, R>(A.lz + a) * (R)A.t[a + g.nxy];
+            if (y + 1 < A.ny && a + A.nx < hi) v += ldf<true, F, R>(A.ly + a) * (R)ld_t<COH>(A.t + a + A.nx);
+            if (z + 1 < A.nz && a + g.nxy < hi) v += ldf<true, F, R>(A.lz + a) * (R)ld_t<COH>(A.t + a + g.nxy);
             ga[k] = (x + 1 < A.nx && a + 1 < hi) ? -di * ldf<true, F, R>(A.lx + a) : R(0);
             de[k] = (R)A.t[a] - di * v;
         }
@@ -250,11 +246,113 @@ __global__ void __launch_bounds__(256) ilu_bwd_kernel(IluArgs A0, const IluArgs 
     }
 }
 
-// ---------------------------------------------------------------- launchers
+// Wavefront form: one launch per diagonal s, one warp per line of it.
+template <int S, typename F>
+__global__ void __launch_bounds__(256) ilu_fwd_kernel(IluArgs A0, const IluArgs *__restrict__ table, int s) {
+    IluArgs a0;
+    if (!ilu_pair(A0, table, a0)) return;
+    const IluView<F> A(a0);
+    const IluGeo g = ilu_geo(A.nx, A.ny, A.nz);
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int y, z;
+    if (!diag_line(g, s, j, y, z)) return;
+    ilu_fwd_line<S, F, false>(A, g, y, z, threadIdx.x & 31);
+}
+
+template <int S, typename F>
+__global__ void __launch_bounds__(256) ilu_bwd_kernel(IluArgs A0, const IluArgs *__restrict__ table, int s) {
+    IluArgs a0;
+    if (!ilu_pair(A0, table, a0)) return;
+    const IluView<F> A(a0);
+    const IluGeo g = ilu_geo(A.nx, A.ny, A.nz);
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int y, z;
+    if (!diag_line(g, s, j, y, z)) return;
+    ilu_bwd_line<S, F, false>(A, g, y, z, threadIdx.x & 31);
+}
+
+// Dataflow form: one cooperative launch per sweep.  Line (s, j) of diagonal s
+// (j-th line, z ascending) is taken by warp (off(s) + j) mod W, so every warp
+// meets its lines in diagonal order and waits only on lines of earlier
+// diagonals, which earlier work of other warps produces: with every warp
+// resident (cooperative launch) the sweep cannot deadlock.  A line waits for
+// its two predecessors' ready flags (forward: y-1 and z-1; backward: y+1 and
+// z+1), written with release semantics after the line's values; the waits are
+// bounded, and a wait that gives up records FL_TIMEOUT and goes on (the
+// results are then unusable, the kernel still ends).
+constexpr int kFlowSpin = 1 << 22;
+
+__device__ __forceinline__ void flow_wait(const int *f, int *err) {
+    for (int it = 0; it < kFlowSpin; ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+        if (v) return;
+        __nanosleep(32);
+    }
+    atomicOr(err + FL_TIMEOUT, 1);
+}
+
+__device__ __forceinline__ void flow_signal(int *f) {
+    __threadfence();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(f), "r"(1) : "memory");
+}
+
+template <int S, typename F, bool FWD>
+__global__ void __launch_bounds__(256) ilu_flow_kernel(IluArgs a0, int *ready, int *err) {
+    const IluView<F> A(a0);
+    const IluGeo g = ilu_geo(A.nx, A.ny, A.nz);
+    const int lane = threadIdx.x & 31;
+    const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nd = A.ny + A.nz - 1;
+    long long rem = 0;  // (lines in the diagonals before s, in sweep order) mod W
+    for (int q = 0; q < nd; ++q) {
+        const int s = FWD ? q : nd - 1 - q;
+        const int z0 = (s - (A.ny - 1) > 0) ? s - (A.ny - 1) : 0;
+        const int z1 = (s < A.nz - 1) ? s : A.nz - 1;
+        const int len = z1 - z0 + 1;
+        long long j = w - rem;
+        if (j < 0) j += W;
+        for (; j < len; j += W) {
+            const int z = z0 + (int)j, y = s - z;
+            if (FWD) {
+                if (y > 0) flow_wait(ready + (long long)z * A.ny + y - 1, err);
+                if (z > 0) flow_wait(ready + (long long)(z - 1) * A.ny + y, err);
+                ilu_fwd_line<S, F, true>(A, g, y, z, lane);
+            } else {
+                if (y + 1 < A.ny) flow_wait(ready + (long long)z * A.ny + y + 1, err);
+                if (z + 1 < A.nz) flow_wait(ready + (long long)(z + 1) * A.ny + y, err);
+                ilu_bwd_line<S, F, true>(A, g, y, z, lane);
+            }
+            flow_signal(ready + (long long)z * A.ny + y);
+        }
+        rem += len;
+        while (rem >= W) rem -= W;
+    }
+}
+
 static int diag_len(int ny, int nz, int s) {
     const int z0 = (s - (ny - 1) > 0) ? s - (ny - 1) : 0;
     const int z1 = (s < nz - 1) ? s : nz - 1;
     return z1 - z0 + 1;
+}
+
+// Blocks of a cooperative dataflow launch: every block resident (0: not possible).
+template <int S, typename F, bool FWD>
+static int flow_grid() {
+    static int cached = -1;
+    if (cached < 0) {
+        int dev = 0, coop = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ilu_flow_kernel<S, F, FWD>, 256, 0) != cudaSuccess)
+            cached = 0;
+        else
+            cached = coop ? per * sms : 0;
+    }
+    return cached;
 }
 
 template <int S>
@@ -300,6 +398,20 @@ static cudaError_t ilu_solve_s(const KernelCtx &c, const double *r, double *t, c
     a.r = r; a.t = t;
     a.ctl = nullptr;
     const int nd = c.ny + c.nz - 1;
+    const int gf = flow_grid<S, F, true>(), gb = flow_grid<S, F, false>();
+    if (c.ws.ilu_ready && gf > 0 && gb > 0) {
+        // dataflow form: two cooperative launches
+        int *ready = c.ws.ilu_ready, *err = c.ws.flags;
+        void *args[] = {&a, &ready, &err};
+        const size_t fb = sizeof(int) * (size_t)c.ny * c.nz;
+        cudaError_t e = cudaMemsetAsync(ready, 0, fb, st);
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel((const void *)ilu_flow_kernel<S, F, true>, gf, 256, args, 0, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ready, 0, fb, st);
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel((const void *)ilu_flow_kernel<S, F, false>, gb, 256, args, 0, st);
+        return e;
+    }
     for (int s = 0; s < nd; ++s) {
         const int lines = diag_len(c.ny, c.nz, s);
         ilu_fwd_kernel<S, F><<<(lines + 3) / 4, 128, 0, st>>>(a, nullptr, s);
@@ -320,6 +432,28 @@ static cudaError_t ilu_table_s(const IluArgs *table, int npairs, int ndiag, int 
     for (int s = 0; s < ndiag; ++s) ilu_fwd_kernel<S, F><<<grid, 32 * warps, 0, st>>>(none, table, s);
     for (int s = ndiag - 1; s >= 0; --s) ilu_bwd_kernel<S, F><<<grid, 32 * warps, 0, st>>>(none, table, s);
     return cudaGetLastError();
+}
+
+template <typename F>
+static long long ilu_launches_t(const KernelCtx &c) {
+    switch (ilu_slots(c.nx)) {
+#define FFP_CASE(SS)                                                                          \
+    case SS:                                                                                   \
+        return (c.ws.ilu_ready && flow_grid<SS, F, true>() > 0 && flow_grid<SS, F, false>() > 0) \
+                   ? 2                                                                         \
+                   : 2LL * (c.ny + c.nz - 1);
+        FFP_SLOT_LIST(FFP_CASE)
+#undef FFP_CASE
+        default: return 0;
+    }
+}
+
+long long ilu_solve_launches(const KernelCtx &c) {
+    switch (c.prec) {
+        case FFP_FP64: return ilu_launches_t<double>(c);
+        case FFP_FP32: return ilu_launches_t<float>(c);
+        default: return ilu_launches_t<__nv_bfloat16>(c);
+    }
 }
 
 int ilu_slots(int nx) {

@@ -518,6 +518,8 @@ struct Ws {
     double *sF[2][2];
     double *sW[2][2];
     double *sC[2][3];
+    // ILU(0) dataflow sweeps: ready flag per line [ny * nz]
+    int *ilu_ready;
     // reductions
     double *red;   // partial sums [kRedSlots]
     double *scal;  // scalars [kScal]

@@ -114,6 +114,7 @@ cudaError_t launch_ilu_setup_table(int slots, const IluPivArgs *table, int count
                                    int maxlines, cudaStream_t st);
 cudaError_t launch_ilu_solve(const KernelCtx &c, const double *r, double *t, cudaStream_t st);
 int ilu_slots(int nx);  // lane split of the ILU(0) line sweeps
+long long ilu_solve_launches(const KernelCtx &c);  // kernels one launch_ilu_solve launches
 
 // One pair of the ILU(0) solve t = B_ILU0^{-1} r; factors in storage precision.
 struct IluArgs {
