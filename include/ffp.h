@@ -179,8 +179,13 @@ int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, dou
  * loads the library holds until the process exits.
  *   h       handle from ffp_setup; its device must be the current device
  *   r, z    device FP64 [N], distinct (as for ffp_apply)
- * Returns FFP_ERR_ARG if nx * ny > FFP_NOALLOC_MAX_PLANE (the grid's planes do
- * not fit the fixed scratch) or if the current device is not the handle's.
+ * Returns FFP_ERR_ARG if the grid's planes do not fit the fixed scratch -- if
+ * nx * ny > FFP_NOALLOC_MAX_PLANE, or if one plane in the apply's line-block
+ * layout (ny * 32 * (S + 1) values of its arithmetic type, FP64 for FP64
+ * factors, FP32 otherwise; S = the smallest of 1, 2, 3, 4, 6, 8, 11, 16, 22,
+ * 32 with 16 S >= nx - 1 - floor((nx - 1) / 2)) takes more than
+ * FFP_NOALLOC_MAX_PLANE * 8 bytes -- or if the current device is not the
+ * handle's.
  * The first call on a device looks up the array's device address; make that
  * first call before any stream capture on that device.  All calls share the
  * one array: calls whose kernels overlap on the GPU (on different streams, or

@@ -69,8 +69,14 @@ size_t ffp::carve_workspace(const ffp_grid *g, int prec, int S_force, char *base
     w.r = (double *)take(8 * n); w.z = (double *)take(8 * n);
     w.p = (double *)take(8 * n); w.q = (double *)take(8 * n);
     w.c1 = (double *)take(8 * n); w.c2 = (double *)take(8 * n);
-    if (prec != FFP_FP64) { w.r32 = (float *)take(4 * n); w.z32 = (float *)take(4 * n); }
-    w.ascr = (double *)take(8 * 2 * nxy);
+    {
+        // the apply's vectors in the line-block layout, in its arithmetic type
+        const size_t ab = (prec == FFP_FP64) ? 8 : 4;
+        const size_t lb = (size_t)lb_len(S > 0 ? S : 1);
+        w.ra = take(ab * nlines * lb);
+        w.za = take(ab * nlines * lb);
+        w.ascr = take(ab * 2 * (size_t)g->ny * lb);
+    }
     for (int h = 0; h < 2; ++h) {
         for (int pp = 0; pp < 2; ++pp)
             for (int b = 0; b < 3; ++b) w.sP[h][pp][b] = (double *)take(8 * nxy);
@@ -94,10 +100,11 @@ constexpr size_t kScalBytes = 8 * (size_t)kScal + 4 * 16;
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? FFP_OK : FFP_ERR_CUDA; }
 
-// kernels launched by one B_NTD apply / one ILU(0) solve
+// kernels launched by one B_NTD apply (conversions to and from the line-block
+// layout around the sweeps) / one ILU(0) solve
 long long ntd_launches(const KernelCtx &c) {
     const int mz = (c.nz - 1) / 2;
-    return ((mz > 0 || c.nz - 1 - mz > 0) ? 3 : 1) + (c.prec != FFP_FP64 ? 2 : 0);
+    return ((mz > 0 || c.nz - 1 - mz > 0) ? 3 : 1) + 2;
 }
 long long ilu_launches(const KernelCtx &c) { return ilu_solve_launches(c); }
 
@@ -115,9 +122,8 @@ cudaError_t precond_apply(const KernelCtx &c, const double *r, double *z, cudaSt
         // B_c^{-1} r = y + B_NTD^{-1} (r - A y), y = B_ILU0^{-1} r
         if (e == cudaSuccess) e = launch_ilu_solve(c, r, c.ws.c1, st);
         if (e == cudaSuccess) e = launch_resid_vec(c, r, c.ws.c1, c.ws.c2, st);
-        if (e == cudaSuccess) e = launch_apply(c, c.ws.c2, z, st, ev ? ev + 1 : nullptr);
-        if (e == cudaSuccess) e = launch_add(c, z, c.ws.c1, st);
-        *launches += ilu_launches(c) + 2 + ntd_launches(c);
+        if (e == cudaSuccess) e = launch_apply(c, c.ws.c2, z, st, ev ? ev + 1 : nullptr, c.ws.c1);
+        *launches += ilu_launches(c) + 1 + ntd_launches(c);
     }
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[3], st);
     return e;
@@ -372,7 +378,13 @@ int noalloc_scratch(int device, double **out) {
 
 extern "C" int ffp_apply_noalloc(ffp_handle *h, const double *r, double *z, void *stream) {
     if (!h || !r || !z || r == z) return FFP_ERR_ARG;
-    if ((long long)h->c.nx * h->c.ny > FFP_NOALLOC_MAX_PLANE) return FFP_ERR_ARG;
+    // one scratch plane (line-block layout, the apply's arithmetic type) must fit
+    // FFP_NOALLOC_MAX_PLANE FP64 values
+    const long long plane_bytes = (long long)h->c.ny * lb_len(h->c.slots) *
+                                  (h->c.prec == FFP_FP64 ? 8 : 4);
+    if ((long long)h->c.nx * h->c.ny > FFP_NOALLOC_MAX_PLANE ||
+        plane_bytes > 8LL * FFP_NOALLOC_MAX_PLANE)
+        return FFP_ERR_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return FFP_ERR_CUDA;
     if (dev != h->device) return FFP_ERR_ARG;
@@ -380,6 +392,6 @@ extern "C" int ffp_apply_noalloc(ffp_handle *h, const double *r, double *z, void
     const int st = noalloc_scratch(dev, &scr);
     if (st != FFP_OK) return st;
     KernelCtx c = h->c;
-    c.ws.ascr = scr;
+    c.ws.ascr = static_cast<void *>(scr);
     return cuda_status(launch_apply(c, r, z, (cudaStream_t)stream));
 }

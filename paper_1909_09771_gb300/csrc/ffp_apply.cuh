@@ -18,13 +18,16 @@
 //
 // Latency hiding (warp specialisation).  Each of the two compute warps walks
 // a fixed sequence of line steps -- per plane its lower-sweep lines, the twist
-// line, its upper-sweep lines -- and has a producer warp (warps 2 and 3) that
-// walks the same sequence ahead of it.  The producer copies what step g reads
-// into stage g mod NST of a ring in shared memory with cp.async:
-//   * the factor line records (coupling, 1/M, l2, l3 fields and the twist
-//     cell) as 16-byte chunks shared by its lanes;
-//   * the vector rows of the step as one 8-byte copy per cell, lane l copying
-//     the cells compute lane l owns;
+// line, its upper-sweep lines -- and has two producer warps that walk the same
+// sequence ahead of it, taking its steps in turn.  The producer copies what step g reads
+// into stage g mod NST of a ring in shared memory:
+//   * the factor line records (alpha, gamma, 1/M of the line, the l2 field of
+//     the line it couples to in the plane, the l3 field of the line it couples
+//     to across planes, and their twist cells);
+//   * the vector rows of the step -- every vector the sweeps read or write is
+//     kept in the line-block layout (lb_pos), the register layout of the line
+//     solve, so a row is one contiguous block;
+// all as 16-byte cp.async chunks spread over its lanes (coalesced),
 // and signals the stage's "full" mbarrier when its copies complete; the
 // compute warp waits on it, computes, and releases the stage on its "empty"
 // mbarrier.  All the address arithmetic thus stays off the compute warp's
@@ -67,12 +70,6 @@ struct ApplyView {
           z(static_cast<R *>(a.z)), scr(static_cast<R *>(a.scr)), flags(a.flags) {}
 };
 
-__device__ __forceinline__ void cp_async_elem(float *dst, const float *src) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src));
-}
-__device__ __forceinline__ void cp_async_elem(double *dst, const double *src) { cp_async8(dst, src); }
-
 constexpr int kSmemBudget = 220 * 1024;
 
 // Compile-time stage layout for phase PH: fields [NF][32 S] F, twist-cell
@@ -108,8 +105,16 @@ struct Stage {
 // One CTA per level-3 half (phases 0, 2) or per twist plane (phase 1) of one
 // pair: the pair is A0, or table[blockIdx.y] when a table is given; a pair
 // whose control word is given and has bit 0 clear returns at once.
+// Warps 0 and 1 compute the two level-2 halves.  Compute warp c has two
+// producer warps, 2 + c and 6 + c, which stage its steps in turn (step g by
+// producer g mod 2).  A warp runs on scheduler partition warp mod 4, so the
+// producers share partitions 2 and 3 and leave partitions 0 and 1 to the
+// compute warps; warps 4 and 5 (partitions 0 and 1) only help initialise.
+constexpr int kProducers = 2;
+constexpr int kApplyThreads = 256;
+
 template <int S, typename F, int PH>
-__global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const ApplyArgs *__restrict__ table) {
+__global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, const ApplyArgs *__restrict__ table) {
     using R = typename Compute<F>::type;
     const ApplyArgs &src = table ? table[blockIdx.y] : A0;
     if (src.ctl && !(*src.ctl & 1)) return;  // a batched pair that does not iterate now
@@ -119,8 +124,10 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
     static_assert(SG::total(NST, VST, FFP_MAX_NX) <= kSmemBudget, "stage ring does not fit");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool producer = warp >= 2;
-    const int wid = warp & 1;  // the level-2 half this warp computes or feeds
+    const bool idle = (warp == 4 || warp == 5);
+    const bool producer = warp >= 2 && !idle;
+    const int wid = warp & 1;                  // the level-2 half this warp computes or feeds
+    const int ppar = (warp >= 6) ? 1 : 0;      // the steps this producer stages (g mod 2)
     const int nx = A.nx, ny = A.ny, nz = A.nz;
     const int nxy = nx * ny;
     const LineMap L(nx);
@@ -146,11 +153,13 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    if (idle) return;
     bool aborted = false;
     int cell[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) cell[s] = (s < cnt) ? slot_cell<S>(L, lane, s) : 0;
     const long RL = rec_len(S);
+    const long BL = lb_len(S);  // values per line block of a vector
 
     // plane of chain position pl, the plane whose output it couples to (-1: none), coupling plane
     auto plane_of = [&](int pl, int &i, int &other, int &cpl) {
@@ -172,7 +181,7 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
     // future-step cursor: chain plane fpl, step fs within the plane, global step fg
     int fpl = 0, fs = 0, fg = 0;
     auto issue_next = [&]() {
-        if (fpl < npl) {
+        if (fpl < npl && fg % kProducers == ppar) {
             const int slot = fg % NST, use = fg / NST;
             if (use > 0 && !aborted && !mbar_wait(empty + slot, (use - 1) & 1)) {
                 aborted = true;
@@ -185,42 +194,43 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
             const int t = (kind == 0) ? fs : ((kind == 1) ? nl : 2 * nl - fs);
             const int k = (kind == 1) ? my : line_of(t);
             const long own = (long)i * ny + k;
-            long l2r = -1, l3a = -1, l3b = -1;
+            long l2r = -1, l3a = -1;
             if (kind == 0) { if (t > 0) l2r = (long)i * ny + ((wid == 0) ? k - 1 : k); }
             else if (kind == 1) { if (nl > 0) l2r = (long)i * ny + ((wid == 0) ? my - 1 : my); }
             else l2r = (long)i * ny + ((wid == 0) ? k : k - 1);
-            const long row = (long)i * nxy + (long)k * nx;
+            const long bown = own * BL;
             const R *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;
             if (PH == 0) {
                 if (kind != 2) {
                     if (other >= 0) l3a = (long)cpl * ny + k;
-                    v0 = A.r + row;
-                    if (kind == 0 && other >= 0 && 2 * t + 1 > D) v1 = A.z + (long)other * nxy + (long)k * nx;
+                    v0 = A.r + bown;
+                    if (kind == 0 && other >= 0 && 2 * t + 1 > D) v1 = A.z + ((long)other * ny + k) * BL;
                 } else if (2 * (nl - t) > D) {
-                    v0 = A.z + row;
+                    v0 = A.z + bown;
                 }
             } else if (PH == 1) {
                 if (kind != 2) {
-                    v0 = A.r + row;
-                    if (mz > 0) { l3a = (long)(mz - 1) * ny + k; v1 = A.z + row - nxy; }
-                    if (mz < nz - 1) { l3b = (long)mz * ny + k; v2 = A.z + row + nxy; }
+                    v0 = A.r + bown;
+                    if (mz > 0) { l3a = (long)(mz - 1) * ny + k; v1 = A.z + bown - (long)ny * BL; }
+                    if (mz < nz - 1) v2 = A.z + bown + (long)ny * BL;
                 } else if (2 * (nl - t) > D) {
-                    v0 = A.z + row;
+                    v0 = A.z + bown;
                 }
             } else {
                 if (kind != 2) {
                     l3a = (long)cpl * ny + k;
                     // the first plane's neighbour is the twist plane, written by the previous launch
-                    if (fpl == 0 || (kind == 0 && 2 * t + 1 > D)) v0 = A.z + (long)other * nxy + (long)k * nx;
-                    if (kind == 1) v1 = A.z + row;  // y of the twist line
+                    if (fpl == 0 || (kind == 0 && 2 * t + 1 > D)) v0 = A.z + ((long)other * ny + k) * BL;
+                    if (kind == 1) v1 = A.z + bown;  // y of the twist line
                 } else {
-                    if (2 * (nl - t) > D) v0 = A.scr + (long)h * nxy + (long)k * nx;
-                    v1 = A.z + row;                 // y, written by phase 0/1
+                    if (2 * (nl - t) > D) v0 = A.scr + ((long)h * ny + k) * BL;
+                    v1 = A.z + bown;                 // y, written by phase 0/1
                 }
             }
-            // stage fields: [0..2] own alpha, gamma, minv, [3] l2 row, [4] l3a
-            // (the twist-plane phase's second coupling l3b is read from l3n)
-            (void)l3b;
+            // factor records: stage fields [0..2] own alpha, gamma, minv, [3] l2 field of
+            // row l2r, [4] l3 field of row l3a (the twist-plane phase's second coupling
+            // is read from l3n), as 16-byte chunks spread over the lanes; twist-cell
+            // blocks [0] own, [1] l2r, [2] l3a
             const long src[5] = {own, own, own, l2r, l3a};
             const int fld[5] = {REC_ALPHA, REC_GAMMA, REC_MINV, REC_L2, REC_L3};
             constexpr int CH = SG::kFld / 16;
@@ -235,7 +245,6 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
                             cp_async16(st + f * SG::kFld + (c0 + lane) * 16, gp + (c0 + lane) * 16);
                 }
             }
-            // twist-cell blocks: [0] own, [1] l2 row, [2] l3a
             constexpr int MC = SG::kMid / 16;
             if (lane < NM * MC) {
                 const int j = lane / MC, c = lane % MC;
@@ -247,14 +256,15 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
             }
             if (VST) {
                 const R *vs[3] = {v0, v1, v2};
+                constexpr int VC = SG::kVec / 16;  // 16-byte chunks of one row block
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     if (vs[v]) {
-                        R *dst = reinterpret_cast<R *>(st + SG::kVecOff + v * SG::kVec);
+                        unsigned char *dst = st + SG::kVecOff + v * SG::kVec;
+                        const unsigned char *src = reinterpret_cast<const unsigned char *>(vs[v]);
 #pragma unroll
-                        for (int s = 0; s < S; ++s)
-                            if (s < cnt) cp_async_elem(dst + s * 32 + lane, vs[v] + cell[s]);
-                        cp_async_elem(dst + S * 32 + lane, vs[v] + L.m);
+                        for (int c0 = 0; c0 < VC; c0 += 32)
+                            if (c0 + lane < VC) cp_async16(dst + (c0 + lane) * 16, src + (c0 + lane) * 16);
                     }
                 }
             }
@@ -278,19 +288,18 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
     auto M_ = [&](const unsigned char *st, int j, int w) -> R {
         return to_r(reinterpret_cast<const F *>(st + NF * SG::kFld + j * SG::kMid)[w], R());
     };
+    // staged vector row v, slot s (s == S: the twist cell, position 32 S of the block)
     auto V_ = [&](const unsigned char *st, int v, int s) -> R {
-        return reinterpret_cast<const R *>(st + SG::kVecOff + v * SG::kVec)[s * 32 + lane];
+        return reinterpret_cast<const R *>(st + SG::kVecOff + v * SG::kVec)[s < S ? s * 32 + lane : S * 32];
     };
-    // vector slots of pads are never copied into: zero them once so that every
-    // slot can be computed without a validity test (their factors are 0 / 1)
-    if (VST) {
-        for (int q = 0; q < NST * NV; ++q) {
-            R *vb = reinterpret_cast<R *>(ring + (q / NV) * SG::kBytes + SG::kVecOff + (q % NV) * SG::kVec);
+    // the same from a row block in global memory
+    auto G_ = [&](const R *blk, int s) -> R { return blk[s < S ? s * 32 + lane : S * 32]; };
+    // store a row block: valid slots, zero pads, the twist cell from lane 0
+    auto put = [&](R *blk, const R (&x)[S], R xm) {
 #pragma unroll
-            for (int s = 0; s < S; ++s)
-                if (s >= cnt) vb[s * 32 + lane] = R(0);
-        }
-    }
+        for (int s = 0; s < S; ++s) blk[s * 32 + lane] = (s < cnt) ? x[s] : R(0);
+        blk[S * 32 + lane] = (lane == 0) ? xm : R(0);
+    };
 #pragma unroll
     for (int s = 0; s <= S; ++s) tcache[s * 32 + lane] = R(0);
     __syncwarp();
@@ -322,31 +331,32 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
         twisted_solve_pre<S, R>(al, ga, mi, M_(st, 0, MID_MINV), M_(st, 0, MID_EM1), M_(st, 0, MID_EM),
                                 cnt, lane, b, bm, x, xm);
     };
-    // plane right-hand side v of cell slot s (s == S: twist cell) of a lower or
-    // twist step; NEAR: the coupled plane's row is read from global memory
+    // plane right-hand side v of slot s (s == S: twist cell) of a lower or twist
+    // step of the line with block offset bk (natural row offset nrow); zrow = the
+    // coupled plane's row block; NEAR: that row is read from global memory
     const int nzv = nz;
-    auto rhs_v = [&](const unsigned char *st, int s, long row, const R *zrow, bool near,
+    auto rhs_v = [&](const unsigned char *st, int s, long bk, long nrow, const R *zrow, bool near,
                      bool twist, int pl, int other) -> R {
         const int a = (s == S) ? L.m : cell[s];
         const R c3 = (s < S) ? F_(st, 4, s) : M_(st, 2, MID_L3);
         R v;
         if (PH == 0) {
-            v = VST ? V_(st, 0, s) : A.r[row + a];
+            v = VST ? V_(st, 0, s) : G_(A.r + bk, s);
             if (other >= 0) {
-                const R yp = twist ? tcache[s * 32 + lane] : ((VST && !near) ? V_(st, 1, s) : zrow[a]);
+                const R yp = twist ? tcache[s * 32 + lane] : ((VST && !near) ? V_(st, 1, s) : G_(zrow, s));
                 v -= c3 * yp;
             }
         } else if (PH == 1) {
-            v = VST ? V_(st, 0, s) : A.r[row + a];
-            if (mz > 0) v -= c3 * (VST ? V_(st, 1, s) : A.z[row - nxy + a]);
+            v = VST ? V_(st, 0, s) : G_(A.r + bk, s);
+            if (mz > 0) v -= c3 * (VST ? V_(st, 1, s) : G_(A.z + bk - (long)ny * BL, s));
             if (mz < nzv - 1) {
-                const R c4 = to_r(A.l3n[row + a], R());   // coupling mz <-> mz+1
-                v -= c4 * (VST ? V_(st, 2, s) : A.z[row + nxy + a]);
+                const R c4 = to_r(A.l3n[nrow + a], R());   // coupling mz <-> mz+1
+                v -= c4 * (VST ? V_(st, 2, s) : G_(A.z + bk + (long)ny * BL, s));
             }
         } else {
             R za;
             if (twist && pl > 0) za = tcache[s * 32 + lane];
-            else za = (VST && (!near || pl == 0)) ? V_(st, 0, s) : zrow[a];
+            else za = (VST && (!near || pl == 0)) ? V_(st, 0, s) : G_(zrow, s);
             v = c3 * za;
         }
         return v;
@@ -356,34 +366,31 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
         int i, other, cpl;
         plane_of(pl, i, other, cpl);
         R *gbuf = gbase + (pl & 1) * 2 * nx;
-        const long pbase = (long)i * nxy;
-        const R *zo = (other >= 0) ? A.z + (long)other * nxy : A.z;
-        R *scrp = A.scr + (long)h * nxy;
+        const long pbase = (long)i * nxy;                  // natural offset of plane i
+        const long pblk = (long)i * ny * BL;               // block offset of plane i
+        const long oblk = (other >= 0) ? (long)other * ny * BL : 0;
+        R *scrp = A.scr + (long)h * ny * BL;
         // ------------------------------------------------------------ lower sweep
         // steps t < TN read the coupled plane's row directly (written fewer than NST steps ago)
         constexpr int TN = (D + 1) / 2;
         auto lower = [&](int t, bool near) {
             const unsigned char *st = begin();
             const int k = line_of(t);
-            const long row = pbase + (long)k * nx;
-            const R *zrow = zo + (long)k * nx;
+            const long bk = pblk + (long)k * BL, nrow = pbase + (long)k * nx;
+            const R *zrow = A.z + oblk + (long)k * BL;
             R b[S], bm;
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                b[s] = rhs_v(st, s, row, zrow, near, false, pl, other);
+                b[s] = rhs_v(st, s, bk, nrow, zrow, near, false, pl, other);
                 if (t > 0) b[s] -= F_(st, 3, s) * w[s];
             }
-            bm = rhs_v(st, S, row, zrow, near, false, pl, other);
+            bm = rhs_v(st, S, bk, nrow, zrow, near, false, pl, other);
             if (t > 0) bm -= M_(st, 1, MID_L2) * wm;
             R x[S], xm;
             solve(st, b, bm, x, xm);
-            R *out = (PH == 2) ? scrp + (long)k * nx : A.z + row;
+            put((PH == 2) ? scrp + (long)k * BL : A.z + bk, x, xm);
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                if (s < cnt) out[cell[s]] = x[s];
-                w[s] = x[s];
-            }
-            if (lane == 0) out[L.m] = xm;
+            for (int s = 0; s < S; ++s) w[s] = x[s];
             wm = xm;
             finish();
         };
@@ -396,8 +403,8 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
         R u[S], um;
         {
             const unsigned char *st = begin();
-            const long row = pbase + (long)my * nx;
-            const R *zrow = zo + (long)my * nx;
+            const long bk = pblk + (long)my * BL, nrow = pbase + (long)my * nx;
+            const R *zrow = A.z + oblk + (long)my * BL;
             R *gw = gbuf + wid * nx;
 #pragma unroll
             for (int s = 0; s < S; ++s)
@@ -405,8 +412,8 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
             if (lane == 0) gw[L.m] = (nl > 0) ? M_(st, 1, MID_L2) * wm : R(0);
             R b[S], bm;
 #pragma unroll
-            for (int s = 0; s < S; ++s) b[s] = rhs_v(st, s, row, zrow, false, true, pl, other);
-            bm = rhs_v(st, S, row, zrow, false, true, pl, other);
+            for (int s = 0; s < S; ++s) b[s] = rhs_v(st, s, bk, nrow, zrow, false, true, pl, other);
+            bm = rhs_v(st, S, bk, nrow, zrow, false, true, pl, other);
             named_barrier(1, 64);
 #pragma unroll
             for (int s = 0; s < S; ++s)
@@ -414,15 +421,16 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
             bm = bm - gbuf[L.m] - gbuf[nx + L.m];
             solve(st, b, bm, u, um);
             // final value of the twist line: u (phases 0, 1) or y - u (phase 2)
+            R f[S], fm;
 #pragma unroll
             for (int s = 0; s <= S; ++s) {
-                const int a = (s == S) ? L.m : cell[s];
                 const R uu = (s < S) ? u[s] : um;
                 R fin = uu;
-                if (PH == 2) fin = (VST ? V_(st, 1, s) : A.z[row + a]) - uu;
+                if (PH == 2) fin = (VST ? V_(st, 1, s) : G_(A.z + bk, s)) - uu;
                 tcache[s * 32 + lane] = fin;
-                if (wid == 0 && ((s < S && s < cnt) || (s == S && lane == 0))) A.z[row + a] = fin;
+                if (s < S) f[s] = fin; else fm = fin;
             }
+            if (wid == 0) put(A.z + bk, f, fm);
             finish();
         }
         // ------------------------------------------------------------ upper sweep
@@ -430,24 +438,24 @@ __global__ void __launch_bounds__(128, 1) apply_kernel(ApplyArgs A0, const Apply
         auto upper = [&](int t, bool near) {
             const unsigned char *st = begin();
             const int k = line_of(t);
-            const long row = pbase + (long)k * nx;
+            const long bk = pblk + (long)k * BL;
             R b[S], bm;
 #pragma unroll
             for (int s = 0; s < S; ++s) b[s] = F_(st, 3, s) * u[s];
             bm = M_(st, 1, MID_L2) * um;
             R x[S], xm;
             solve(st, b, bm, x, xm);
-            const R *wrow = (PH == 2) ? scrp + (long)k * nx : A.z + row;
+            const R *wrow = (PH == 2) ? scrp + (long)k * BL : A.z + bk;
+            R f[S], fm;
 #pragma unroll
             for (int s = 0; s <= S; ++s) {
-                const int a = (s == S) ? L.m : cell[s];
-                const R wv = (VST && !near) ? V_(st, 0, s) : wrow[a];
+                const R wv = (VST && !near) ? V_(st, 0, s) : G_(wrow, s);
                 const R uu = wv - ((s < S) ? x[s] : xm);
                 R fin = uu;
-                if (PH == 2) fin = (VST ? V_(st, 1, s) : A.z[row + a]) - uu;
-                if ((s < S && s < cnt) || (s == S && lane == 0)) A.z[row + a] = fin;
-                if (s < S) u[s] = uu; else um = uu;
+                if (PH == 2) fin = (VST ? V_(st, 1, s) : G_(A.z + bk, s)) - uu;
+                if (s < S) { u[s] = uu; f[s] = fin; } else { um = uu; fm = fin; }
             }
+            put(A.z + bk, f, fm);
             finish();
         };
         {
@@ -468,14 +476,13 @@ static cudaError_t launch_phase(const ApplyArgs &a, const ApplyArgs *table, int 
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(apply_kernel<S, F, PH>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    apply_kernel<S, F, PH><<<grid, 128, smem, st>>>(a, table);
+    apply_kernel<S, F, PH><<<grid, kApplyThreads, smem, st>>>(a, table);
     return cudaGetLastError();
 }
 
 template <int S, typename F>
 cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
-                            const cudaEvent_t *ev) {
-    using R = typename Compute<F>::type;
+                            const cudaEvent_t *ev, const double *add) {
     ApplyArgs a;
     a.nx = c.nx; a.ny = c.ny; a.nz = c.nz;
     a.rec = c.ws.rec;
@@ -483,15 +490,9 @@ cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cuda
     a.scr = c.ws.ascr;
     a.flags = c.ws.flags;
     a.ctl = nullptr;
-    cudaError_t e = cudaSuccess;
-    if constexpr (sizeof(R) == 8) {
-        a.r = r;
-        a.z = z;
-    } else {
-        a.r = c.ws.r32;
-        a.z = c.ws.z32;
-        e = launch_to_f32(c, r, c.ws.r32, st);
-    }
+    a.r = c.ws.ra;
+    a.z = c.ws.za;
+    cudaError_t e = launch_to_lb(c, r, c.ws.ra, st);
     const int mz = (a.nz - 1) / 2;
     const bool halves = (mz > 0) || (a.nz - 1 - mz > 0);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
@@ -499,9 +500,7 @@ cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cuda
     if (e == cudaSuccess) e = launch_phase<S, F, 1>(a, nullptr, c.nx, dim3(1), st);
     if (e == cudaSuccess && halves) e = launch_phase<S, F, 2>(a, nullptr, c.nx, dim3(2), st);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
-    if constexpr (sizeof(R) == 4) {
-        if (e == cudaSuccess) e = launch_from_f32(c, c.ws.z32, z, st);
-    }
+    if (e == cudaSuccess) e = launch_from_lb(c, c.ws.za, z, add, st);
     return e;
 }
 

@@ -48,7 +48,8 @@ struct PairArgs {
     const double *b;
     double *x;                        // caller's vectors
     double *r, *z, *p, *q, *c1, *c2;  // CG vectors and B_c temporaries
-    float *r32, *z32;                 // FP32 apply input and output
+    void *ra, *za;                    // apply input and output, line-block layout (lb_pos)
+    int S;                            // line slot count of the instance
     double *red, *scal;
     int *flags;
     const int *ctl;                   // control word
@@ -99,27 +100,35 @@ __global__ void b_finalize(const PairArgs *__restrict__ T, int need, int mode, i
     finalize_scalars(mode, P.nb, (c & CTL_FRESH) ? 1 : 0, flexible, P.red, P.scal, P.flags);
 }
 
-// preconditioner input: B_c's c2 = r - A c1 (c1 = B_ILU0^{-1} r), then the FP32 copy
-__global__ void __launch_bounds__(kThreads) b_prec_in(const PairArgs *__restrict__ T, int combo, int f32) {
+// preconditioner input, in the apply's line-block layout and arithmetic type R:
+// B_c's r - A c1 (c1 = B_ILU0^{-1} r), or r
+template <typename R>
+__global__ void __launch_bounds__(kThreads) b_prec_in(const PairArgs *__restrict__ T, int combo) {
     PairArgs P;
     int c;
     if (!pair_of(T, CTL_ITER, P, c)) return;
     const Geo g = pgeo(P);
+    R *ra = static_cast<R *>(P.ra);
+    const long long L = lb_len(P.S);
     FFP_PAIR_LOOP(P, a) {
         const double v = combo ? P.r[a] - stencil(g, a, P.d, P.cx, P.cy, P.cz, P.c1) : P.r[a];
-        if (f32) P.r32[a] = (float)v;
-        else P.c2[a] = v;
+        const long long line = a / P.nx;
+        ra[line * L + lb_pos(P.nx, P.S, (int)(a - line * P.nx))] = (R)v;
     }
 }
 
-// preconditioner output: z = f64(z32) (FP32 apply), then z += c1 (B_c)
-__global__ void __launch_bounds__(kThreads) b_prec_out(const PairArgs *__restrict__ T, int combo, int f32) {
+// preconditioner output: z = the apply's output (+ c1 for B_c)
+template <typename R>
+__global__ void __launch_bounds__(kThreads) b_prec_out(const PairArgs *__restrict__ T, int combo) {
     PairArgs P;
     int c;
     if (!pair_of(T, CTL_ITER, P, c)) return;
+    const R *za = static_cast<const R *>(P.za);
+    const long long L = lb_len(P.S);
     FFP_PAIR_LOOP(P, a) {
-        const double za = f32 ? (double)P.z32[a] : P.z[a];
-        P.z[a] = combo ? za + P.c1[a] : za;
+        const long long line = a / P.nx;
+        const double v = (double)za[line * L + lb_pos(P.nx, P.S, (int)(a - line * P.nx))];
+        P.z[a] = combo ? v + P.c1[a] : v;
     }
 }
 
@@ -194,10 +203,12 @@ bool grid_ok(const ffp_grid &g) {
            (long long)g.nx * g.ny * g.nz <= 2000000000LL;
 }
 
-// vectors of a pair beyond an instance's first: r z p q c1 c2, r32 z32, apply scratch, partials
+// vectors of a pair beyond an instance's first: r z p q c1 c2, the apply input and output
+// blocks, apply scratch (line-block layout), partials
 size_t extra_pair_bytes(const ffp_grid &g, int prec) {
-    const size_t n = (size_t)g.nx * g.ny * g.nz, nxy = (size_t)g.nx * g.ny;
-    return 6 * al256(8 * n) + (prec != FFP_FP64 ? 2 * al256(4 * n) : 0) + al256(16 * nxy) +
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const size_t ab = (prec == FFP_FP64) ? 8 : 4, lb = (size_t)lb_len(slots_for(g.nx));
+    return 6 * al256(8 * n) + 2 * al256(ab * (size_t)g.ny * g.nz * lb) + al256(ab * 2 * (size_t)g.ny * lb) +
            al256(8 * (size_t)kRedSlots);
 }
 
@@ -210,7 +221,8 @@ struct Group {
 long long kernel_count_of(const std::vector<Group> &gs, int combo, int f32) {
     long long k = 0;
     for (const Group &g : gs)
-        k += (combo ? 2LL * g.ndiag : 0) + ((combo || f32) ? 2 : 0) + 3 + 7;
+        k += (combo ? 2LL * g.ndiag : 0) + 2 + 3 + 7;
+    (void)f32;
     return k;
 }
 
@@ -272,7 +284,8 @@ size_t batch_layout(int count, const ffp_grid *grids, int nrhs, int prec, char *
         char *wbase = take(wsb);
         if (B) carve_workspace(&grids[i], prec, 0, wbase, &B->inst[i].ws);
         const ffp_grid &g = grids[i];
-        const size_t n = (size_t)g.nx * g.ny * g.nz, nxy = (size_t)g.nx * g.ny;
+        const size_t n = (size_t)g.nx * g.ny * g.nz;
+        const size_t ab = (prec == FFP_FP64) ? 8 : 4, lb = (size_t)lb_len(slots_for(g.nx));
         for (int j = 0; j < nrhs; ++j) {
             const int up = i * nrhs + j;  // caller's pair index
             if (j == 0) {
@@ -280,7 +293,7 @@ size_t batch_layout(int count, const ffp_grid *grids, int nrhs, int prec, char *
                     const Ws &w = B->inst[i].ws;
                     PairArgs &P = B->pairs[up];
                     P.r = w.r; P.z = w.z; P.p = w.p; P.q = w.q; P.c1 = w.c1; P.c2 = w.c2;
-                    P.r32 = w.r32; P.z32 = w.z32; P.red = w.red;
+                    P.ra = w.ra; P.za = w.za; P.red = w.red;
                     (*ascr)[up] = w.ascr;
                 }
                 continue;
@@ -292,8 +305,9 @@ size_t batch_layout(int count, const ffp_grid *grids, int nrhs, int prec, char *
                 auto sub = [&](size_t bytes) { char *p = pb + o; o += al256(bytes); return p; };
                 P.r = (double *)sub(8 * n); P.z = (double *)sub(8 * n); P.p = (double *)sub(8 * n);
                 P.q = (double *)sub(8 * n); P.c1 = (double *)sub(8 * n); P.c2 = (double *)sub(8 * n);
-                if (prec != FFP_FP64) { P.r32 = (float *)sub(4 * n); P.z32 = (float *)sub(4 * n); }
-                (*ascr)[up] = sub(16 * nxy);
+                P.ra = sub(ab * (size_t)g.ny * g.nz * lb);
+                P.za = sub(ab * (size_t)g.ny * g.nz * lb);
+                (*ascr)[up] = sub(ab * 2 * (size_t)g.ny * lb);
                 P.red = (double *)sub(8 * (size_t)kRedSlots);
             }
         }
@@ -312,9 +326,15 @@ cudaError_t group_precond(const ffp_batch *B, const Group &g, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     if (combo)
         e = launch_ilu_table(B->prec, g.Si, B->dilu + g.p0, g.np, g.ndiag, g.maxlines, B->cfg.ilu_warps, s);
-    if (e == cudaSuccess && (combo || f32)) b_prec_in<<<gv, kThreads, 0, s>>>(T, combo, f32);
-    if (e == cudaSuccess) e = launch_apply_table(B->prec, g.S, B->dapply + g.p0, g.np, g.nx_max, s);
-    if (e == cudaSuccess && (combo || f32)) b_prec_out<<<gv, kThreads, 0, s>>>(T, combo, f32);
+    if (e == cudaSuccess) {
+        if (f32) b_prec_in<float><<<gv, kThreads, 0, s>>>(T, combo);
+        else b_prec_in<double><<<gv, kThreads, 0, s>>>(T, combo);
+        e = launch_apply_table(B->prec, g.S, B->dapply + g.p0, g.np, g.nx_max, s);
+    }
+    if (e == cudaSuccess) {
+        if (f32) b_prec_out<float><<<gv, kThreads, 0, s>>>(T, combo);
+        else b_prec_out<double><<<gv, kThreads, 0, s>>>(T, combo);
+    }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -618,6 +638,7 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
         PairArgs P = B->pairs[up];
         P.nx = c.nx; P.ny = c.ny; P.nz = c.nz; P.nxy = c.nx * c.ny; P.n = c.n;
         P.nb = grid_for(c.n);
+        P.S = c.slots;
         P.d = c.ws.d; P.cx = c.ws.cx; P.cy = c.ws.cy; P.cz = c.ws.cz;
         P.b = nullptr; P.x = nullptr;
         P.scal = reinterpret_cast<double *>(B->dscal + kPairScal * k);
@@ -627,8 +648,8 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
         ApplyArgs &A = at[k];
         A.nx = c.nx; A.ny = c.ny; A.nz = c.nz;
         A.rec = c.ws.rec; A.l3n = c.ws.l3;
-        if (precision != FFP_FP64) { A.r = P.r32; A.z = P.z32; }
-        else { A.r = (precond == FFP_PRECOND_COMBO) ? P.c2 : P.r; A.z = P.z; }
+        A.r = P.ra;
+        A.z = P.za;
         A.scr = ascr[up];
         A.flags = P.flags;
         A.ctl = P.ctl;
@@ -664,6 +685,11 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->dilu, it.data(), sizeof(IluArgs) * B->npairs, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->dctl, 0, 4 * (size_t)B->npairs, st);
+    // padding positions of the apply input blocks must read 0; b_prec_in writes only cells
+    for (int k = 0; k < B->npairs && e == cudaSuccess; ++k) {
+        const PairArgs &P = pt[k];
+        e = cudaMemsetAsync(P.ra, 0, (precision == FFP_FP64 ? 8 : 4) * (size_t)P.ny * P.nz * lb_len(P.S), st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     // ---- streams and events of the graphs
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->gs, cudaStreamNonBlocking);

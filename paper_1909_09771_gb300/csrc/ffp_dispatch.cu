@@ -10,7 +10,7 @@ template <int S> cudaError_t setup_for_slots(const KernelCtx &, const double *, 
 template <int S> cudaError_t setup_table_for_slots(const SetupArgs *, int, int, cudaStream_t);
 template <int S, typename F>
 cudaError_t apply_for_slots(const KernelCtx &, const double *, double *, cudaStream_t,
-                            const cudaEvent_t *);
+                            const cudaEvent_t *, const double *);
 template <int S, typename F>
 cudaError_t apply_table_for_slots(const ApplyArgs *, int, int, cudaStream_t);
 
@@ -35,9 +35,9 @@ cudaError_t launch_setup_table(int slots, const SetupArgs *table, int count, int
 
 template <typename F>
 static cudaError_t apply_t(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
-                           const cudaEvent_t *ev) {
+                           const cudaEvent_t *ev, const double *add) {
     switch (c.slots) {
-#define FFP_CASE(SS) case SS: return apply_for_slots<SS, F>(c, r, z, st, ev);
+#define FFP_CASE(SS) case SS: return apply_for_slots<SS, F>(c, r, z, st, ev, add);
         FFP_SLOT_LIST(FFP_CASE)
 #undef FFP_CASE
         default: return cudaErrorInvalidValue;
@@ -45,11 +45,11 @@ static cudaError_t apply_t(const KernelCtx &c, const double *r, double *z, cudaS
 }
 
 cudaError_t launch_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
-                         const cudaEvent_t *ev) {
+                         const cudaEvent_t *ev, const double *add) {
     switch (c.prec) {
-        case FFP_FP64: return apply_t<double>(c, r, z, st, ev);
-        case FFP_FP32: return apply_t<float>(c, r, z, st, ev);
-        case FFP_BF16: return apply_t<__nv_bfloat16>(c, r, z, st, ev);
+        case FFP_FP64: return apply_t<double>(c, r, z, st, ev, add);
+        case FFP_FP32: return apply_t<float>(c, r, z, st, ev, add);
+        case FFP_BF16: return apply_t<__nv_bfloat16>(c, r, z, st, ev, add);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -246,6 +246,147 @@ __device__ __forceinline__ void ilu_bwd_line(const IluView<F> &A, const IluGeo &
     }
 }
 
+// The same two sweeps split for the dataflow form: everything a line reads that
+// no other line writes (1/D, the bands, r) is loaded before its predecessors'
+// flags are awaited, so only the t reads and the scan stay on the critical path.
+template <int S, typename F>
+struct IluLinePre {
+    using R = typename Compute<F>::type;
+    R di[S], cx[S], cy[S], cz[S], rv[S];
+};
+
+template <int S, typename F>
+__device__ __forceinline__ void ilu_fwd_pre(const IluView<F> &A, const IluGeo &g, int y, int z,
+                                            int lane, IluLinePre<S, F> &P) {
+    using R = typename Compute<F>::type;
+    const long long base = (long long)A.nx * y + g.nxy * z;
+    int cnt = A.nx - lane * S;
+    cnt = cnt < 0 ? 0 : (cnt > S ? S : cnt);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        P.di[k] = R(0); P.cx[k] = R(0); P.cy[k] = R(0); P.cz[k] = R(0); P.rv[k] = R(0);
+        if (k < cnt) {
+            const int x = lane * S + k;
+            const long long a = base + x;
+            const long long lo = (a < g.M) ? 0 : g.M;
+            P.di[k] = ldf<true, F, R>(A.dinv + a);
+            P.rv[k] = (R)__ldg(A.r + a);
+            if (y > 0 && a - A.nx >= lo) P.cy[k] = ldf<true, F, R>(A.ly + a - A.nx);
+            if (z > 0 && a - g.nxy >= lo) P.cz[k] = ldf<true, F, R>(A.lz + a - g.nxy);
+            if (x > 0 && a - 1 >= lo) P.cx[k] = ldf<true, F, R>(A.lx + a - 1);
+        }
+    }
+}
+
+// same arithmetic, in the same order, as ilu_fwd_line
+template <int S, typename F>
+__device__ __forceinline__ void ilu_fwd_fin(const IluView<F> &A, const IluGeo &g, int y, int z,
+                                            int lane, const IluLinePre<S, F> &P) {
+    using R = typename Compute<F>::type;
+    const long long base = (long long)A.nx * y + g.nxy * z;
+    int cnt = A.nx - lane * S;
+    cnt = cnt < 0 ? 0 : (cnt > S ? S : cnt);
+    R al[S], be[S];
+    R Am = R(1), B = R(0);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        al[k] = R(1); be[k] = R(0);
+        if (k < cnt) {
+            const int x = lane * S + k;
+            const long long a = base + x;
+            const long long lo = (a < g.M) ? 0 : g.M;
+            const R di = P.di[k];
+            R v = P.rv[k];
+            if (y > 0 && a - A.nx >= lo) v -= P.cy[k] * (R)ld_t<true>(A.t + a - A.nx);
+            if (z > 0 && a - g.nxy >= lo) v -= P.cz[k] * (R)ld_t<true>(A.t + a - g.nxy);
+            al[k] = (x > 0 && a - 1 >= lo) ? -di * P.cx[k] : R(0);
+            be[k] = di * v;
+        }
+        B = fma(al[k], B, be[k]);
+        Am = Am * al[k];
+    }
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+        const R Au = __shfl_up_sync(FULL, Am, dd);
+        const R Bu = __shfl_up_sync(FULL, B, dd);
+        if (lane >= dd) { B = fma(Am, Bu, B); Am = Am * Au; }
+    }
+    R c = __shfl_up_sync(FULL, B, 1);
+    if (lane == 0) c = R(0);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        c = fma(al[k], c, be[k]);
+        if (k < cnt) A.t[base + lane * S + k] = (double)c;
+    }
+}
+
+template <int S, typename F>
+__device__ __forceinline__ void ilu_bwd_pre(const IluView<F> &A, const IluGeo &g, int y, int z,
+                                            int lane, IluLinePre<S, F> &P) {
+    using R = typename Compute<F>::type;
+    const long long base = (long long)A.nx * y + g.nxy * z;
+    int cnt = A.nx - lane * S;
+    cnt = cnt < 0 ? 0 : (cnt > S ? S : cnt);
+#pragma unroll
+    for (int k = S - 1; k >= 0; --k) {
+        P.di[k] = R(0); P.cx[k] = R(0); P.cy[k] = R(0); P.cz[k] = R(0); P.rv[k] = R(0);
+        if (k < cnt) {
+            const int x = lane * S + k;
+            const long long a = base + x;
+            const long long hi = (a < g.M) ? g.M : g.n;
+            P.di[k] = ldf<true, F, R>(A.dinv + a);
+            if (y + 1 < A.ny && a + A.nx < hi) P.cy[k] = ldf<true, F, R>(A.ly + a);
+            if (z + 1 < A.nz && a + g.nxy < hi) P.cz[k] = ldf<true, F, R>(A.lz + a);
+            if (x + 1 < A.nx && a + 1 < hi) P.cx[k] = ldf<true, F, R>(A.lx + a);
+            P.rv[k] = (R)A.t[a];  // this line's forward value (previous launch)
+        }
+    }
+}
+
+// same arithmetic, in the same order, as ilu_bwd_line
+template <int S, typename F>
+__device__ __forceinline__ void ilu_bwd_fin(const IluView<F> &A, const IluGeo &g, int y, int z,
+                                            int lane, const IluLinePre<S, F> &P) {
+    using R = typename Compute<F>::type;
+    const long long base = (long long)A.nx * y + g.nxy * z;
+    int cnt = A.nx - lane * S;
+    cnt = cnt < 0 ? 0 : (cnt > S ? S : cnt);
+    R ga[S], de[S];
+    R G = R(1), B = R(0);
+#pragma unroll
+    for (int k = S - 1; k >= 0; --k) {
+        ga[k] = R(1); de[k] = R(0);
+        if (k < cnt) {
+            const int x = lane * S + k;
+            const long long a = base + x;
+            const long long hi = (a < g.M) ? g.M : g.n;
+            const R di = P.di[k];
+            R v = R(0);
+            if (y + 1 < A.ny && a + A.nx < hi) v += P.cy[k] * (R)ld_t<true>(A.t + a + A.nx);
+            if (z + 1 < A.nz && a + g.nxy < hi) v += P.cz[k] * (R)ld_t<true>(A.t + a + g.nxy);
+            ga[k] = (x + 1 < A.nx && a + 1 < hi) ? -di * P.cx[k] : R(0);
+            de[k] = P.rv[k] - di * v;
+        }
+        B = fma(ga[k], B, de[k]);
+        G = G * ga[k];
+    }
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+        const R Gd = __shfl_down_sync(FULL, G, dd);
+        const R Bd = __shfl_down_sync(FULL, B, dd);
+        if (lane + dd < 32) { B = fma(G, Bd, B); G = G * Gd; }
+    }
+    R c = __shfl_down_sync(FULL, B, 1);
+    if (lane == 31) c = R(0);
+#pragma unroll
+    for (int k = S - 1; k >= 0; --k) {
+        c = fma(ga[k], c, de[k]);
+        if (k < cnt) A.t[base + lane * S + k] = (double)c;
+    }
+}
+
 // Wavefront form: one launch per diagonal s, one warp per line of it.
 template <int S, typename F>
 __global__ void __launch_bounds__(256) ilu_fwd_kernel(IluArgs A0, const IluArgs *__restrict__ table, int s) {
@@ -287,7 +428,6 @@ __device__ __forceinline__ void flow_wait(const int *f, int *err) {
         int v;
         asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
         if (v) return;
-        __nanosleep(32);
     }
     atomicOr(err + FL_TIMEOUT, 1);
 }
@@ -316,14 +456,17 @@ __global__ void __launch_bounds__(256) ilu_flow_kernel(IluArgs a0, int *ready, i
         if (j < 0) j += W;
         for (; j < len; j += W) {
             const int z = z0 + (int)j, y = s - z;
+            IluLinePre<S, F> P;
             if (FWD) {
+                ilu_fwd_pre<S, F>(A, g, y, z, lane, P);
                 if (y > 0) flow_wait(ready + (long long)z * A.ny + y - 1, err);
                 if (z > 0) flow_wait(ready + (long long)(z - 1) * A.ny + y, err);
-                ilu_fwd_line<S, F, true>(A, g, y, z, lane);
+                ilu_fwd_fin<S, F>(A, g, y, z, lane, P);
             } else {
+                ilu_bwd_pre<S, F>(A, g, y, z, lane, P);
                 if (y + 1 < A.ny) flow_wait(ready + (long long)z * A.ny + y + 1, err);
                 if (z + 1 < A.nz) flow_wait(ready + (long long)(z + 1) * A.ny + y, err);
-                ilu_bwd_line<S, F, true>(A, g, y, z, lane);
+                ilu_bwd_fin<S, F>(A, g, y, z, lane, P);
             }
             flow_signal(ready + (long long)z * A.ny + y);
         }

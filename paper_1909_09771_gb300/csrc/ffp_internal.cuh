@@ -404,6 +404,33 @@ enum { MID_MINV = 0, MID_EM1 = 1, MID_EM = 2, MID_L2 = 3, MID_L3 = 4, REC_NMID =
 
 __host__ __device__ __forceinline__ long rec_len(int S) { return (long)REC_NFIELD * 32 * S + REC_NMID; }
 
+// Line-block layout of the apply's vectors: every line of nx cells is a block
+// of 32 (S + 1) values; position s * 32 + lane holds the cell of slot s of that
+// lane (the register layout of the line solve), position 32 S the twist cell,
+// every other position 0.  Each block is one contiguous, 16-byte aligned row.
+__host__ __device__ __forceinline__ long lb_len(int S) { return 32L * (S + 1); }
+
+__host__ __device__ __forceinline__ long lb_pos(int nx, int S, int a) {
+    const int m = (nx - 1) / 2;
+    if (a == m) return 32L * S;
+    int c, lane;
+    if (a < m) { c = a; lane = c / S; }
+    else { c = nx - 1 - a; lane = 16 + c / S; }
+    return (long)(c % S) * 32 + lane;
+}
+
+// Cell of position p of a line block, or -1 for a padding position.
+__host__ __device__ __forceinline__ int lb_cell(int nx, int S, int p) {
+    const int s = p >> 5, lane = p & 31;
+    const int m = (nx - 1) / 2;
+    if (s == S) return lane == 0 ? m : -1;
+    const int j = lane & 15;
+    const int tot = (lane < 16) ? m : nx - 1 - m;
+    const int c = j * S + s;
+    if (c >= tot) return -1;
+    return (lane < 16) ? c : nx - 1 - c;
+}
+
 // Offset inside a record of field f at cell a of an nx-cell line (the twist
 // cell maps to mid + midf).
 __host__ __device__ __forceinline__ long rec_cell(int nx, int S, int f, int midf, int a) {
@@ -456,6 +483,22 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
 __device__ __forceinline__ void mbar_arrive_cpasync(unsigned long long *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// arrive and add `bytes` to the transaction count of the current phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
+// completion reported to the mbarrier as transaction bytes
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // One bounded try of the phase with the given parity (acquire at CTA scope).
 __device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parity) {
     unsigned ok;
@@ -508,10 +551,11 @@ struct Ws {
     double *c1, *c2;
     // CG vectors
     double *r, *z, *p, *q;
-    // FP32 copies of the apply's input and output (FP32/BF16 factors only)
-    float *r32, *z32;
-    // apply scratch: 2 planes (one per level-3 half) of FP64
-    double *ascr;
+    // the apply's input and output in the line-block layout (lb_pos), in the
+    // apply's arithmetic type (FP64 for FP64 factors, FP32 otherwise)
+    void *ra, *za;
+    // apply scratch: 2 planes (one per level-3 half), line-block layout, same type
+    void *ascr;
     // setup scratch, per half h: P bands ping-pong [h][pp][3], FP64 line factors of the
     // current plane [h][2] (l1, minv), w/v/beta plane [h][2], correction to the twist plane [h][3]
     double *sP[2][2][3];

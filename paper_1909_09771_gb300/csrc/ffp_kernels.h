@@ -34,8 +34,11 @@ cudaError_t launch_convert_bands(const KernelCtx &c, cudaStream_t st);  // l3 (a
 cudaError_t launch_resid_vec(const KernelCtx &c, const double *r, const double *y, double *w,
                              cudaStream_t st);                           // w = r - A y
 cudaError_t launch_add(const KernelCtx &c, double *z, const double *y, cudaStream_t st);  // z += y
-cudaError_t launch_to_f32(const KernelCtx &c, const double *x, float *y, cudaStream_t st);
-cudaError_t launch_from_f32(const KernelCtx &c, const float *x, double *y, cudaStream_t st);
+// natural-order FP64 x -> the apply's line-block layout in its arithmetic type (ws.ra
+// layout), and back (y = value + add, add optional)
+cudaError_t launch_to_lb(const KernelCtx &c, const double *x, void *xb, cudaStream_t st);
+cudaError_t launch_from_lb(const KernelCtx &c, const void *xb, double *y, const double *add,
+                           cudaStream_t st);
 cudaError_t launch_spmv(const KernelCtx &c, const double *x, double *y, cudaStream_t st);
 cudaError_t launch_export(const KernelCtx &c, const void *src, double *dst, cudaStream_t st);
 // natural-order band from the factor records: 0 = l1, 1 = 1/M, 2 = l2, 3 = l3
@@ -78,7 +81,8 @@ cudaError_t launch_setup_table(int slots, const SetupArgs *table, int count, int
                                cudaStream_t st);
 
 // One (instance, right-hand side) pair of the NTD apply.  Vectors r, z, scr are
-// in the compute type (FP64 for FP64 factors, FP32 otherwise).
+// in the line-block layout (lb_pos) and the compute type (FP64 for FP64
+// factors, FP32 otherwise).
 struct ApplyArgs {
     int nx, ny, nz;
     const void *rec;  // factor line records
@@ -94,10 +98,10 @@ struct ApplyArgs {
 cudaError_t launch_apply_table(int prec, int slots, const ApplyArgs *table, int npairs, int nx_max,
                                cudaStream_t st);
 
-// ffp_dispatch.cu: z = B_NTD^{-1} r; ev (optional) = two events recorded just
-// before and just after the three sweep launches
+// ffp_dispatch.cu: z = B_NTD^{-1} r (+ add, optional); ev (optional) = two events
+// recorded just before and just after the three sweep launches
 cudaError_t launch_apply(const KernelCtx &c, const double *r, double *z, cudaStream_t st,
-                         const cudaEvent_t *ev = nullptr);
+                         const cudaEvent_t *ev = nullptr, const double *add = nullptr);
 
 // ffp_ilu.cu: ILU(0) of blkD(A) (pivots in D64 scratch, 1/D stored) and t = B_ILU0^{-1} r
 cudaError_t launch_ilu_setup(const KernelCtx &c, double *D64, cudaStream_t st);

@@ -120,18 +120,32 @@ __global__ void __launch_bounds__(kThreads) add_kernel(long long n, double *z,
         z[a] += y[a];
 }
 
-__global__ void __launch_bounds__(kThreads) to_f32_kernel(long long n, const double *__restrict__ x,
-                                                         float *y) {
-    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
-         a += (long long)gridDim.x * blockDim.x)
-        y[a] = (float)x[a];
+// natural FP64 -> line-block layout of type R (one thread per block position;
+// padding positions are written as 0)
+template <typename R>
+__global__ void __launch_bounds__(kThreads) to_lb_kernel(long long nlines, int nx, int S,
+                                                        const double *__restrict__ x, R *y) {
+    const long long L = lb_len(S);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nlines * L;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long line = e / L;
+        const int a = lb_cell(nx, S, (int)(e - line * L));
+        y[e] = (a >= 0) ? (R)x[line * nx + a] : R(0);
+    }
 }
 
-__global__ void __launch_bounds__(kThreads) from_f32_kernel(long long n, const float *__restrict__ x,
-                                                           double *y) {
+// line-block layout of type R -> natural FP64 (+ add)
+template <typename R>
+__global__ void __launch_bounds__(kThreads) from_lb_kernel(long long n, int nx, int S,
+                                                          const R *__restrict__ xb, double *y,
+                                                          const double *__restrict__ add) {
+    const long long L = lb_len(S);
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
-         a += (long long)gridDim.x * blockDim.x)
-        y[a] = (double)x[a];
+         a += (long long)gridDim.x * blockDim.x) {
+        const long long line = a / nx;
+        const double v = (double)xb[line * L + lb_pos(nx, S, (int)(a - line * nx))];
+        y[a] = add ? v + add[a] : v;
+    }
 }
 
 // r = b - A x ; partials (r.r, b.b)
@@ -314,13 +328,22 @@ cudaError_t launch_add(const KernelCtx &c, double *z, const double *y, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_f32(const KernelCtx &c, const double *x, float *y, cudaStream_t st) {
-    to_f32_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, x, y);
+cudaError_t launch_to_lb(const KernelCtx &c, const double *x, void *xb, cudaStream_t st) {
+    const long long nlines = (long long)c.ny * c.nz;
+    const long long tot = nlines * lb_len(c.slots);
+    if (c.prec == FFP_FP64)
+        to_lb_kernel<double><<<grid_for(tot), kThreads, 0, st>>>(nlines, c.nx, c.slots, x, (double *)xb);
+    else
+        to_lb_kernel<float><<<grid_for(tot), kThreads, 0, st>>>(nlines, c.nx, c.slots, x, (float *)xb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_from_f32(const KernelCtx &c, const float *x, double *y, cudaStream_t st) {
-    from_f32_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, x, y);
+cudaError_t launch_from_lb(const KernelCtx &c, const void *xb, double *y, const double *add,
+                           cudaStream_t st) {
+    if (c.prec == FFP_FP64)
+        from_lb_kernel<double><<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.nx, c.slots, (const double *)xb, y, add);
+    else
+        from_lb_kernel<float><<<grid_for(c.n), kThreads, 0, st>>>(c.n, c.nx, c.slots, (const float *)xb, y, add);
     return cudaGetLastError();
 }
 
