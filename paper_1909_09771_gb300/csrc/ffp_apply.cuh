@@ -72,18 +72,71 @@ struct ApplyView {
 
 constexpr int kSmemBudget = 220 * 1024;
 
-// Compile-time stage layout for phase PH: fields [NF][32 S] F, twist-cell
-// blocks [NM][8] F, vectors [NV][S+1][32] R.
+// The S slots of one lane from p (16-byte aligned, lane-major layout) with
+// vector loads, converted to the compute type R.
+template <int S, typename T, typename R>
+__device__ __forceinline__ void ld_slots(const T *p, R (&o)[S]) {
+    constexpr int SP = slot_pitch(S);
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < SP / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4 *>(p)[q];
+            if (4 * q + 0 < S) o[4 * q + 0] = (R)v.x;
+            if (4 * q + 1 < S) o[4 * q + 1] = (R)v.y;
+            if (4 * q + 2 < S) o[4 * q + 2] = (R)v.z;
+            if (4 * q + 3 < S) o[4 * q + 3] = (R)v.w;
+        }
+    } else if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int q = 0; q < SP / 2; ++q) {
+            const double2 v = reinterpret_cast<const double2 *>(p)[q];
+            if (2 * q + 0 < S) o[2 * q + 0] = (R)v.x;
+            if (2 * q + 1 < S) o[2 * q + 1] = (R)v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < SP / 4; ++q) {
+            const uint2 u = reinterpret_cast<const uint2 *>(p)[q];
+            const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
+            const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
+            if (4 * q + 0 < S) o[4 * q + 0] = (R)__low2float(a);
+            if (4 * q + 1 < S) o[4 * q + 1] = (R)__high2float(a);
+            if (4 * q + 2 < S) o[4 * q + 2] = (R)__low2float(b);
+            if (4 * q + 3 < S) o[4 * q + 3] = (R)__high2float(b);
+        }
+    }
+}
+
+// Store the S slots of one lane (slots >= cnt and the pitch padding as 0) with
+// vector stores; p 16-byte aligned.
+template <int S, typename R>
+__device__ __forceinline__ void st_slots(R *p, const R (&x)[S], int cnt) {
+    constexpr int SP = slot_pitch(S);
+    auto val = [&](int s) -> R { return (s < S && s < cnt) ? x[s < S ? s : 0] : R(0); };
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int q = 0; q < SP / 4; ++q)
+            reinterpret_cast<float4 *>(p)[q] = make_float4(val(4 * q), val(4 * q + 1), val(4 * q + 2), val(4 * q + 3));
+    } else {
+#pragma unroll
+        for (int q = 0; q < SP / 2; ++q)
+            reinterpret_cast<double2 *>(p)[q] = make_double2(val(2 * q), val(2 * q + 1));
+    }
+}
+
+// Compile-time stage layout for phase PH: fields [NF][32][SP] F, twist-cell
+// blocks [NM][8] F, vector row blocks [NV][32 SP + 32] R (SP = slot_pitch(S)).
 template <int S, typename F, int PH>
 struct Stage {
     using R = typename Compute<F>::type;
     static constexpr int NF = 5;  // alpha, gamma, minv, l2, l3
     static constexpr int NM = 3;  // twist-cell blocks: own, l2, l3
     static constexpr int NV = (PH == 1) ? 3 : 2;
-    static constexpr int kFld = 32 * S * (int)sizeof(F);
+    static constexpr int SP = slot_pitch(S);
+    static constexpr int kFld = 32 * SP * (int)sizeof(F);
     static constexpr int kMid = 8 * (int)sizeof(F);
     static constexpr int kVecOff = ((NF * kFld + NM * kMid + 15) / 16) * 16;
-    static constexpr int kVec = (S + 1) * 32 * (int)sizeof(R);
+    static constexpr int kVec = (32 * SP + 32) * (int)sizeof(R);
     // twist caches + full/empty mbarriers of both rings
     static constexpr int kExtra = 2 * (S + 1) * 32 * (int)sizeof(R) + 2 * 2 * 5 * 8;
     __host__ __device__ static constexpr int bytes_v(int vst) { return kVecOff + (vst ? NV * kVec : 0); }
@@ -238,7 +291,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
             for (int f = 0; f < NF; ++f) {
                 if (src[f] >= 0) {
                     const unsigned char *gp = reinterpret_cast<const unsigned char *>(
-                        A.rec + src[f] * RL + (long)fld[f] * 32 * S);
+                        A.rec + src[f] * RL + rec_slot(S, fld[f], 0, 0));
 #pragma unroll
                     for (int c0 = 0; c0 < CH; c0 += 32)
                         if (c0 + lane < CH)
@@ -251,8 +304,8 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
                 const long msrc = (j == 0) ? own : ((j == 1) ? l2r : l3a);
                 if (msrc >= 0)
                     cp_async16(st + NF * SG::kFld + j * SG::kMid + c * 16,
-                               reinterpret_cast<const unsigned char *>(A.rec + msrc * RL +
-                                                                       (long)REC_NFIELD * 32 * S) + c * 16);
+                               reinterpret_cast<const unsigned char *>(A.rec + msrc * RL + rec_mid(S)) +
+                                   c * 16);
             }
             if (VST) {
                 const R *vs[3] = {v0, v1, v2};
@@ -281,24 +334,26 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
     }
 
     // ------------------------------------------------------------------ compute
-    // stage accessors (fields, twist-cell blocks, vectors)
-    auto F_ = [&](const unsigned char *st, int f, int s) -> R {
-        return to_r(reinterpret_cast<const F *>(st + f * SG::kFld)[s * 32 + lane], R());
+    constexpr int SP = SG::SP;
+    // this lane's slots of stage field f; the stage's twist-cell blocks; vector row v
+    auto Fp = [&](const unsigned char *st, int f) -> const F * {
+        return reinterpret_cast<const F *>(st + f * SG::kFld) + lane * SP;
     };
     auto M_ = [&](const unsigned char *st, int j, int w) -> R {
         return to_r(reinterpret_cast<const F *>(st + NF * SG::kFld + j * SG::kMid)[w], R());
     };
-    // staged vector row v, slot s (s == S: the twist cell, position 32 S of the block)
-    auto V_ = [&](const unsigned char *st, int v, int s) -> R {
-        return reinterpret_cast<const R *>(st + SG::kVecOff + v * SG::kVec)[s < S ? s * 32 + lane : S * 32];
+    auto Vp = [&](const unsigned char *st, int v) -> const R * {
+        return reinterpret_cast<const R *>(st + SG::kVecOff + v * SG::kVec);
     };
-    // the same from a row block in global memory
-    auto G_ = [&](const R *blk, int s) -> R { return blk[s < S ? s * 32 + lane : S * 32]; };
+    // a row block (staged or in global memory): this lane's slots and the twist cell
+    auto ldrow = [&](const R *blk, R (&o)[S], R &om) {
+        ld_slots<S>(blk + lane * SP, o);
+        om = blk[32 * SP];
+    };
     // store a row block: valid slots, zero pads, the twist cell from lane 0
     auto put = [&](R *blk, const R (&x)[S], R xm) {
-#pragma unroll
-        for (int s = 0; s < S; ++s) blk[s * 32 + lane] = (s < cnt) ? x[s] : R(0);
-        blk[S * 32 + lane] = (lane == 0) ? xm : R(0);
+        st_slots<S>(blk + lane * SP, x, cnt);
+        blk[32 * SP + lane] = (lane == 0) ? xm : R(0);
     };
 #pragma unroll
     for (int s = 0; s <= S; ++s) tcache[s * 32 + lane] = R(0);
@@ -326,40 +381,66 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
     // the line solve of a step from its stage
     auto solve = [&](const unsigned char *st, const R (&b)[S], R bm, R (&x)[S], R &xm) {
         R al[S], ga[S], mi[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) { al[s] = F_(st, 0, s); ga[s] = F_(st, 1, s); mi[s] = F_(st, 2, s); }
+        ld_slots<S>(Fp(st, 0), al);
+        ld_slots<S>(Fp(st, 1), ga);
+        ld_slots<S>(Fp(st, 2), mi);
         twisted_solve_pre<S, R>(al, ga, mi, M_(st, 0, MID_MINV), M_(st, 0, MID_EM1), M_(st, 0, MID_EM),
                                 cnt, lane, b, bm, x, xm);
     };
-    // plane right-hand side v of slot s (s == S: twist cell) of a lower or twist
-    // step of the line with block offset bk (natural row offset nrow); zrow = the
-    // coupled plane's row block; NEAR: that row is read from global memory
-    const int nzv = nz;
-    auto rhs_v = [&](const unsigned char *st, int s, long bk, long nrow, const R *zrow, bool near,
-                     bool twist, int pl, int other) -> R {
-        const int a = (s == S) ? L.m : cell[s];
-        const R c3 = (s < S) ? F_(st, 4, s) : M_(st, 2, MID_L3);
-        R v;
+    // plane right-hand side (b, bm) of a lower or twist step of the line with block
+    // offset bk (natural row offset nrow); zrow = the coupled plane's row block;
+    // NEAR: that row is read from global memory
+    auto rhs = [&](const unsigned char *st, long bk, long nrow, const R *zrow, bool near, bool twist,
+                   int pl, int other, R (&b)[S], R &bm) {
+        R c3[S];
+        ld_slots<S>(Fp(st, 4), c3);
+        const R c3m = M_(st, 2, MID_L3);
+        R y[S], ym;
         if (PH == 0) {
-            v = VST ? V_(st, 0, s) : G_(A.r + bk, s);
+            if (VST) ldrow(Vp(st, 0), b, bm); else ldrow(A.r + bk, b, bm);
             if (other >= 0) {
-                const R yp = twist ? tcache[s * 32 + lane] : ((VST && !near) ? V_(st, 1, s) : G_(zrow, s));
-                v -= c3 * yp;
+                if (twist) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) y[s] = tcache[s * 32 + lane];
+                    ym = tcache[S * 32 + lane];
+                } else if (VST && !near) {
+                    ldrow(Vp(st, 1), y, ym);
+                } else {
+                    ldrow(zrow, y, ym);
+                }
+#pragma unroll
+                for (int s = 0; s < S; ++s) b[s] -= c3[s] * y[s];
+                bm -= c3m * ym;
             }
         } else if (PH == 1) {
-            v = VST ? V_(st, 0, s) : G_(A.r + bk, s);
-            if (mz > 0) v -= c3 * (VST ? V_(st, 1, s) : G_(A.z + bk - (long)ny * BL, s));
-            if (mz < nzv - 1) {
-                const R c4 = to_r(A.l3n[nrow + a], R());   // coupling mz <-> mz+1
-                v -= c4 * (VST ? V_(st, 2, s) : G_(A.z + bk + (long)ny * BL, s));
+            if (VST) ldrow(Vp(st, 0), b, bm); else ldrow(A.r + bk, b, bm);
+            if (mz > 0) {
+                if (VST) ldrow(Vp(st, 1), y, ym); else ldrow(A.z + bk - (long)ny * BL, y, ym);
+#pragma unroll
+                for (int s = 0; s < S; ++s) b[s] -= c3[s] * y[s];
+                bm -= c3m * ym;
+            }
+            if (mz < nz - 1) {
+                // coupling mz <-> mz+1 from the natural-order l3 band
+                if (VST) ldrow(Vp(st, 2), y, ym); else ldrow(A.z + bk + (long)ny * BL, y, ym);
+#pragma unroll
+                for (int s = 0; s < S; ++s) b[s] -= to_r(A.l3n[nrow + cell[s]], R()) * y[s];
+                bm -= to_r(A.l3n[nrow + L.m], R()) * ym;
             }
         } else {
-            R za;
-            if (twist && pl > 0) za = tcache[s * 32 + lane];
-            else za = (VST && (!near || pl == 0)) ? V_(st, 0, s) : G_(zrow, s);
-            v = c3 * za;
+            if (twist && pl > 0) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) y[s] = tcache[s * 32 + lane];
+                ym = tcache[S * 32 + lane];
+            } else if (VST && (!near || pl == 0)) {
+                ldrow(Vp(st, 0), y, ym);
+            } else {
+                ldrow(zrow, y, ym);
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) b[s] = c3[s] * y[s];
+            bm = c3m * ym;
         }
-        return v;
     };
 
     for (int pl = 0; pl < npl; ++pl) {
@@ -376,16 +457,16 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
         auto lower = [&](int t, bool near) {
             const unsigned char *st = begin();
             const int k = line_of(t);
-            const long bk = pblk + (long)k * BL, nrow = pbase + (long)k * nx;
-            const R *zrow = A.z + oblk + (long)k * BL;
+            const long bk = pblk + (long)k * BL;
             R b[S], bm;
+            rhs(st, bk, pbase + (long)k * nx, A.z + oblk + (long)k * BL, near, false, pl, other, b, bm);
+            if (t > 0) {
+                R l2[S];
+                ld_slots<S>(Fp(st, 3), l2);
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                b[s] = rhs_v(st, s, bk, nrow, zrow, near, false, pl, other);
-                if (t > 0) b[s] -= F_(st, 3, s) * w[s];
+                for (int s = 0; s < S; ++s) b[s] -= l2[s] * w[s];
+                bm -= M_(st, 1, MID_L2) * wm;
             }
-            bm = rhs_v(st, S, bk, nrow, zrow, near, false, pl, other);
-            if (t > 0) bm -= M_(st, 1, MID_L2) * wm;
             R x[S], xm;
             solve(st, b, bm, x, xm);
             put((PH == 2) ? scrp + (long)k * BL : A.z + bk, x, xm);
@@ -403,17 +484,16 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
         R u[S], um;
         {
             const unsigned char *st = begin();
-            const long bk = pblk + (long)my * BL, nrow = pbase + (long)my * nx;
-            const R *zrow = A.z + oblk + (long)my * BL;
+            const long bk = pblk + (long)my * BL;
             R *gw = gbuf + wid * nx;
+            R l2[S];
+            ld_slots<S>(Fp(st, 3), l2);
 #pragma unroll
             for (int s = 0; s < S; ++s)
-                if (s < cnt) gw[cell[s]] = (nl > 0) ? F_(st, 3, s) * w[s] : R(0);
+                if (s < cnt) gw[cell[s]] = (nl > 0) ? l2[s] * w[s] : R(0);
             if (lane == 0) gw[L.m] = (nl > 0) ? M_(st, 1, MID_L2) * wm : R(0);
             R b[S], bm;
-#pragma unroll
-            for (int s = 0; s < S; ++s) b[s] = rhs_v(st, s, bk, nrow, zrow, false, true, pl, other);
-            bm = rhs_v(st, S, bk, nrow, zrow, false, true, pl, other);
+            rhs(st, bk, pbase + (long)my * nx, A.z + oblk + (long)my * BL, false, true, pl, other, b, bm);
             named_barrier(1, 64);
 #pragma unroll
             for (int s = 0; s < S; ++s)
@@ -422,14 +502,20 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
             solve(st, b, bm, u, um);
             // final value of the twist line: u (phases 0, 1) or y - u (phase 2)
             R f[S], fm;
+            if (PH == 2) {
+                R y[S], ym;
+                if (VST) ldrow(Vp(st, 1), y, ym); else ldrow(A.z + bk, y, ym);
 #pragma unroll
-            for (int s = 0; s <= S; ++s) {
-                const R uu = (s < S) ? u[s] : um;
-                R fin = uu;
-                if (PH == 2) fin = (VST ? V_(st, 1, s) : G_(A.z + bk, s)) - uu;
-                tcache[s * 32 + lane] = fin;
-                if (s < S) f[s] = fin; else fm = fin;
+                for (int s = 0; s < S; ++s) f[s] = y[s] - u[s];
+                fm = ym - um;
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; ++s) f[s] = u[s];
+                fm = um;
             }
+#pragma unroll
+            for (int s = 0; s < S; ++s) tcache[s * 32 + lane] = f[s];
+            tcache[S * 32 + lane] = fm;
             if (wid == 0) put(A.z + bk, f, fm);
             finish();
         }
@@ -439,21 +525,30 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
             const unsigned char *st = begin();
             const int k = line_of(t);
             const long bk = pblk + (long)k * BL;
-            R b[S], bm;
+            R l2[S], b[S], bm;
+            ld_slots<S>(Fp(st, 3), l2);
 #pragma unroll
-            for (int s = 0; s < S; ++s) b[s] = F_(st, 3, s) * u[s];
+            for (int s = 0; s < S; ++s) b[s] = l2[s] * u[s];
             bm = M_(st, 1, MID_L2) * um;
             R x[S], xm;
             solve(st, b, bm, x, xm);
-            const R *wrow = (PH == 2) ? scrp + (long)k * BL : A.z + bk;
-            R f[S], fm;
+            R wv[S], wvm;
+            if (VST && !near) ldrow(Vp(st, 0), wv, wvm);
+            else ldrow((PH == 2) ? scrp + (long)k * BL : A.z + bk, wv, wvm);
 #pragma unroll
-            for (int s = 0; s <= S; ++s) {
-                const R wv = (VST && !near) ? V_(st, 0, s) : G_(wrow, s);
-                const R uu = wv - ((s < S) ? x[s] : xm);
-                R fin = uu;
-                if (PH == 2) fin = (VST ? V_(st, 1, s) : G_(A.z + bk, s)) - uu;
-                if (s < S) { u[s] = uu; f[s] = fin; } else { um = uu; fm = fin; }
+            for (int s = 0; s < S; ++s) u[s] = wv[s] - x[s];
+            um = wvm - xm;
+            R f[S], fm;
+            if (PH == 2) {
+                R y[S], ym;
+                if (VST) ldrow(Vp(st, 1), y, ym); else ldrow(A.z + bk, y, ym);
+#pragma unroll
+                for (int s = 0; s < S; ++s) f[s] = y[s] - u[s];
+                fm = ym - um;
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; ++s) f[s] = u[s];
+                fm = um;
             }
             put(A.z + bk, f, fm);
             finish();

@@ -391,39 +391,53 @@ __device__ __forceinline__ void twisted_pivots(int cnt, int lane, const double (
 // The apply reads the stored factors line by line in the warp's own order, so
 // they are stored as one record per line (i, k), record index i*ny + k, with
 // the multipliers of the twisted line solve precomputed:
-//   field 0 alpha[S][32]  -minv_a * (coupling to the chain predecessor)  (pads 1)
-//   field 1 gamma[S][32]  -minv_a * (coupling towards the twist cell)    (pads 1)
-//   field 2 minv[S][32]   1 / M_a                                        (pads 0)
-//   field 3 l2[S][32]     y-band of P_i: coupling of cell a of line k with line k+1 (pads 0)
-//   field 4 l3[S][32]     z-band of A: coupling of cell a of plane i with plane i+1 (pads 0)
+//   field 0 alpha[32][SP]  -minv_a * (coupling to the chain predecessor)  (pads 1)
+//   field 1 gamma[32][SP]  -minv_a * (coupling towards the twist cell)    (pads 1)
+//   field 2 minv[32][SP]   1 / M_a                                        (pads 0)
+//   field 3 l2[32][SP]     y-band of P_i: coupling of cell a of line k with line k+1 (pads 0)
+//   field 4 l3[32][SP]     z-band of A: coupling of cell a of plane i with plane i+1 (pads 0)
 //   mid[8]                the twist cell: 1/M_m, T[m-1,m], T[m,m+1], l2, l3, 0, 0, 0
-// [s][32] is slot s of lanes 0..31.  A record is a multiple of 16 bytes, so a
-// warp pulls it with 16-byte asynchronous copies.
+// Fields are lane-major, [32][SP] (slot_pitch).  A record is a multiple of 16
+// bytes, so a warp pulls it with 16-byte asynchronous copies.
 enum { REC_ALPHA = 0, REC_GAMMA = 1, REC_MINV = 2, REC_L2 = 3, REC_L3 = 4, REC_NFIELD = 5 };
 enum { MID_MINV = 0, MID_EM1 = 1, MID_EM = 2, MID_L2 = 3, MID_L3 = 4, REC_NMID = 8 };
 
-__host__ __device__ __forceinline__ long rec_len(int S) { return (long)REC_NFIELD * 32 * S + REC_NMID; }
+// Slots per lane rounded up to a multiple of 4: a lane's slots of a field are
+// contiguous and 16-byte aligned, so a lane reads or writes them with vector
+// accesses (lane-major layout [32][SP]).
+__host__ __device__ constexpr int slot_pitch(int S) { return (S + 3) & ~3; }
+
+__host__ __device__ __forceinline__ long rec_len(int S) {
+    return (long)REC_NFIELD * 32 * slot_pitch(S) + REC_NMID;
+}
+// offset of slot s of lane `lane` of field f, and of the twist-cell block
+__host__ __device__ __forceinline__ long rec_slot(int S, int f, int lane, int s) {
+    return ((long)f * 32 + lane) * slot_pitch(S) + s;
+}
+__host__ __device__ __forceinline__ long rec_mid(int S) { return (long)REC_NFIELD * 32 * slot_pitch(S); }
 
 // Line-block layout of the apply's vectors: every line of nx cells is a block
-// of 32 (S + 1) values; position s * 32 + lane holds the cell of slot s of that
-// lane (the register layout of the line solve), position 32 S the twist cell,
+// of 32 SP + 32 values; position lane * SP + s holds the cell of slot s of that
+// lane (the register layout of the line solve), position 32 SP the twist cell,
 // every other position 0.  Each block is one contiguous, 16-byte aligned row.
-__host__ __device__ __forceinline__ long lb_len(int S) { return 32L * (S + 1); }
+__host__ __device__ __forceinline__ long lb_len(int S) { return 32L * slot_pitch(S) + 32; }
 
 __host__ __device__ __forceinline__ long lb_pos(int nx, int S, int a) {
     const int m = (nx - 1) / 2;
-    if (a == m) return 32L * S;
+    if (a == m) return 32L * slot_pitch(S);
     int c, lane;
     if (a < m) { c = a; lane = c / S; }
     else { c = nx - 1 - a; lane = 16 + c / S; }
-    return (long)(c % S) * 32 + lane;
+    return (long)lane * slot_pitch(S) + c % S;
 }
 
 // Cell of position p of a line block, or -1 for a padding position.
 __host__ __device__ __forceinline__ int lb_cell(int nx, int S, int p) {
-    const int s = p >> 5, lane = p & 31;
+    const int SP = slot_pitch(S);
     const int m = (nx - 1) / 2;
-    if (s == S) return lane == 0 ? m : -1;
+    if (p >= 32 * SP) return (p == 32 * SP) ? m : -1;
+    const int lane = p / SP, s = p - lane * SP;
+    if (s >= S) return -1;
     const int j = lane & 15;
     const int tot = (lane < 16) ? m : nx - 1 - m;
     const int c = j * S + s;
@@ -435,11 +449,11 @@ __host__ __device__ __forceinline__ int lb_cell(int nx, int S, int p) {
 // cell maps to mid + midf).
 __host__ __device__ __forceinline__ long rec_cell(int nx, int S, int f, int midf, int a) {
     const int m = (nx - 1) / 2;
-    if (a == m) return (long)REC_NFIELD * 32 * S + midf;
+    if (a == m) return rec_mid(S) + midf;
     int c, lane;
     if (a < m) { c = a; lane = c / S; }
     else { c = nx - 1 - a; lane = 16 + c / S; }
-    return (long)f * 32 * S + (long)(c % S) * 32 + lane;
+    return rec_slot(S, f, lane, c % S);
 }
 
 // ---------------------------------------------------------------- async copies

@@ -175,15 +175,15 @@ __device__ __forceinline__ void store_line(const LineMap &L, int lane, int cnt, 
             mid[o + a] = st.f.minv[s];
             put_factor(l1n, (line0 + k) * nx + a, st.To[s], prec);
         }
-        put_factor(rec, rb + (long)REC_ALPHA * 32 * S + s * 32 + lane, v ? -st.f.minv[s] * st.f.ein[s] : 1.0, prec);
-        put_factor(rec, rb + (long)REC_GAMMA * 32 * S + s * 32 + lane, v ? -st.f.minv[s] * st.f.eout[s] : 1.0, prec);
-        put_factor(rec, rb + (long)REC_MINV * 32 * S + s * 32 + lane, v ? st.f.minv[s] : 0.0, prec);
+        put_factor(rec, rb + rec_slot(S, REC_ALPHA, lane, s), v ? -st.f.minv[s] * st.f.ein[s] : 1.0, prec);
+        put_factor(rec, rb + rec_slot(S, REC_GAMMA, lane, s), v ? -st.f.minv[s] * st.f.eout[s] : 1.0, prec);
+        put_factor(rec, rb + rec_slot(S, REC_MINV, lane, s), v ? st.f.minv[s] : 0.0, prec);
     }
     if (lane == 0) {
         l1d[o + L.m] = st.Tom;
         mid[o + L.m] = st.f.minv_m;
         put_factor(l1n, (line0 + k) * nx + L.m, st.Tom, prec);
-        const long mb = rb + (long)REC_NFIELD * 32 * S;
+        const long mb = rb + rec_mid(S);
         put_factor(rec, mb + MID_MINV, st.f.minv_m, prec);
         put_factor(rec, mb + MID_EM1, st.f.em1, prec);
         put_factor(rec, mb + MID_EM, st.f.em, prec);
