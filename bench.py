@@ -271,7 +271,7 @@ def run_ours(args):
             "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
             "peak_kind": peak_kind,
-            "traffic": None,
+            "traffic": APPLY_TRAFFIC.get((args.workload, args.precision)),
             "algorithmic_bytes_per_apply": algo_bytes,
             "ms_per_apply": ntd_per_apply_ms,
             "dependent_line_solves_per_apply": depth,
@@ -515,6 +515,11 @@ def run_reference(args):
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
+
+# DRAM bytes of one B_NTD apply (the three sweep launches) from an ncu capture of
+# the current kernel (profiles/apply_traffic_grf350_fp32.md), by workload and factor
+# precision; absent = not measured for that kernel.
+APPLY_TRAFFIC = {("grf350", "fp32"): 2678.4e6}
 
 # Iterations B_c flexible CG takes to rtol 1e-8 on each workload (seed 0), as
 # counted by the library's FP64 solve, whose arithmetic matches the oracle's

@@ -85,6 +85,7 @@ size_t ffp::carve_workspace(const ffp_grid *g, int prec, int S_force, char *base
         for (int b = 0; b < 3; ++b) w.sC[h][b] = (double *)take(8 * nxy);
     }
     w.ilu_ready = (int *)take(4 * (size_t)g->ny * g->nz);
+    w.ilu_v = (prec != FFP_FP64) ? take(4 * 2 * n) : nullptr;
     w.red = (double *)take(8 * (size_t)kRedSlots);
     // scalar block and flags are contiguous so one copy brings both back
     w.scal = (double *)take(8 * (size_t)kScal + 4 * 16);

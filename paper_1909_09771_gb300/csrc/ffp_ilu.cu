@@ -14,10 +14,25 @@
 // (pivots), evaluated as lane-local composition + a 32-lane scan + lane-local
 // substitution, lane l holding cells l*S .. l*S+S-1.
 #include <cstring>
+#include <type_traits>
 
-#include "ffp_kernels.h"
+#include "ffp_vecops.cuh"
 
 namespace ffp {
+
+__global__ void __launch_bounds__(kThreads) f64_to_f32_kernel(long long n, const double *__restrict__ x,
+                                                             float *y) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        y[a] = (float)x[a];
+}
+
+__global__ void __launch_bounds__(kThreads) f32_to_f64_kernel(long long n, const float *__restrict__ x,
+                                                             double *y) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        y[a] = (double)x[a];
+}
 
 struct IluGeo {
     int nx, ny, nz;
@@ -132,17 +147,20 @@ __global__ void __launch_bounds__(128) ilu_pivot_kernel(IluPivArgs P0,
 }
 
 // ---------------------------------------------------------------- triangular sweeps
-// Typed view of one pair's IluArgs.
-template <typename F>
+// Typed view of one pair's IluArgs; V = type of r and t (FP64, or the FP32
+// copies the single-instance dataflow forms work on, so that no FP64 <-> FP32
+// conversion sits on their dependency chain; the values are the same).
+template <typename F, typename V = double>
 struct IluView {
     int nx, ny, nz;
     const F *dinv, *lx, *ly, *lz;
-    const double *r;
-    double *t;
+    const V *r;
+    V *t;
     __device__ __forceinline__ explicit IluView(const IluArgs &a)
         : nx(a.nx), ny(a.ny), nz(a.nz), dinv(static_cast<const F *>(a.dinv)),
           lx(static_cast<const F *>(a.lx)), ly(static_cast<const F *>(a.ly)),
-          lz(static_cast<const F *>(a.lz)), r(a.r), t(a.t) {}
+          lz(static_cast<const F *>(a.lz)), r(static_cast<const V *>(a.r)),
+          t(static_cast<V *>(a.t)) {}
 };
 
 // The pair of this CTA (A0, or table[blockIdx.y]); false if it is skipped.
@@ -155,6 +173,11 @@ __device__ __forceinline__ bool ilu_pair(const IluArgs &A0, const IluArgs *table
 // form): through L2, never a stale L1 line.
 template <bool COH>
 __device__ __forceinline__ double ld_t(const double *p) {
+    if constexpr (COH) return __ldcg(p);
+    else return *p;
+}
+template <bool COH>
+__device__ __forceinline__ float ld_t(const float *p) {
     if constexpr (COH) return __ldcg(p);
     else return *p;
 }
@@ -198,7 +221,7 @@ __device__ __forceinline__ void ilu_fwd_line(const IluView<F> &A, const IluGeo &
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         c = fma(al[k], c, be[k]);
-        if (k < cnt) A.t[base + lane * S + k] = (double)c;
+        if (k < cnt) A.t[base + lane * S + k] = static_cast<typename std::remove_pointer<decltype(A.t)>::type>(c);
     }
 }
 
@@ -242,7 +265,7 @@ __device__ __forceinline__ void ilu_bwd_line(const IluView<F> &A, const IluGeo &
 #pragma unroll
     for (int k = S - 1; k >= 0; --k) {
         c = fma(ga[k], c, de[k]);
-        if (k < cnt) A.t[base + lane * S + k] = (double)c;
+        if (k < cnt) A.t[base + lane * S + k] = static_cast<typename std::remove_pointer<decltype(A.t)>::type>(c);
     }
 }
 
@@ -255,8 +278,8 @@ struct IluLinePre {
     R di[S], cx[S], cy[S], cz[S], rv[S];
 };
 
-template <int S, typename F>
-__device__ __forceinline__ void ilu_fwd_pre(const IluView<F> &A, const IluGeo &g, int y, int z,
+template <int S, typename F, typename V>
+__device__ __forceinline__ void ilu_fwd_pre(const IluView<F, V> &A, const IluGeo &g, int y, int z,
                                             int lane, IluLinePre<S, F> &P) {
     using R = typename Compute<F>::type;
     const long long base = (long long)A.nx * y + g.nxy * z;
@@ -279,8 +302,8 @@ __device__ __forceinline__ void ilu_fwd_pre(const IluView<F> &A, const IluGeo &g
 }
 
 // same arithmetic, in the same order, as ilu_fwd_line
-template <int S, typename F>
-__device__ __forceinline__ void ilu_fwd_fin(const IluView<F> &A, const IluGeo &g, int y, int z,
+template <int S, typename F, typename V>
+__device__ __forceinline__ void ilu_fwd_fin(const IluView<F, V> &A, const IluGeo &g, int y, int z,
                                             int lane, const IluLinePre<S, F> &P) {
     using R = typename Compute<F>::type;
     const long long base = (long long)A.nx * y + g.nxy * z;
@@ -317,12 +340,12 @@ __device__ __forceinline__ void ilu_fwd_fin(const IluView<F> &A, const IluGeo &g
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         c = fma(al[k], c, be[k]);
-        if (k < cnt) A.t[base + lane * S + k] = (double)c;
+        if (k < cnt) A.t[base + lane * S + k] = static_cast<typename std::remove_pointer<decltype(A.t)>::type>(c);
     }
 }
 
-template <int S, typename F>
-__device__ __forceinline__ void ilu_bwd_pre(const IluView<F> &A, const IluGeo &g, int y, int z,
+template <int S, typename F, typename V>
+__device__ __forceinline__ void ilu_bwd_pre(const IluView<F, V> &A, const IluGeo &g, int y, int z,
                                             int lane, IluLinePre<S, F> &P) {
     using R = typename Compute<F>::type;
     const long long base = (long long)A.nx * y + g.nxy * z;
@@ -345,8 +368,8 @@ __device__ __forceinline__ void ilu_bwd_pre(const IluView<F> &A, const IluGeo &g
 }
 
 // same arithmetic, in the same order, as ilu_bwd_line
-template <int S, typename F>
-__device__ __forceinline__ void ilu_bwd_fin(const IluView<F> &A, const IluGeo &g, int y, int z,
+template <int S, typename F, typename V>
+__device__ __forceinline__ void ilu_bwd_fin(const IluView<F, V> &A, const IluGeo &g, int y, int z,
                                             int lane, const IluLinePre<S, F> &P) {
     using R = typename Compute<F>::type;
     const long long base = (long long)A.nx * y + g.nxy * z;
@@ -383,7 +406,7 @@ __device__ __forceinline__ void ilu_bwd_fin(const IluView<F> &A, const IluGeo &g
 #pragma unroll
     for (int k = S - 1; k >= 0; --k) {
         c = fma(ga[k], c, de[k]);
-        if (k < cnt) A.t[base + lane * S + k] = (double)c;
+        if (k < cnt) A.t[base + lane * S + k] = static_cast<typename std::remove_pointer<decltype(A.t)>::type>(c);
     }
 }
 
@@ -438,9 +461,9 @@ __device__ __forceinline__ void flow_signal(int *f) {
     if ((threadIdx.x & 31) == 0) asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(f), "r"(1) : "memory");
 }
 
-template <int S, typename F, bool FWD>
+template <int S, typename F, bool FWD, typename V>
 __global__ void __launch_bounds__(256) ilu_flow_kernel(IluArgs a0, int *ready, int *err) {
-    const IluView<F> A(a0);
+    const IluView<F, V> A(a0);
     const IluGeo g = ilu_geo(A.nx, A.ny, A.nz);
     const int lane = threadIdx.x & 31;
     const long long W = (long long)gridDim.x * (blockDim.x >> 5);
@@ -458,15 +481,15 @@ __global__ void __launch_bounds__(256) ilu_flow_kernel(IluArgs a0, int *ready, i
             const int z = z0 + (int)j, y = s - z;
             IluLinePre<S, F> P;
             if (FWD) {
-                ilu_fwd_pre<S, F>(A, g, y, z, lane, P);
+                ilu_fwd_pre<S, F, V>(A, g, y, z, lane, P);
                 if (y > 0) flow_wait(ready + (long long)z * A.ny + y - 1, err);
                 if (z > 0) flow_wait(ready + (long long)(z - 1) * A.ny + y, err);
-                ilu_fwd_fin<S, F>(A, g, y, z, lane, P);
+                ilu_fwd_fin<S, F, V>(A, g, y, z, lane, P);
             } else {
-                ilu_bwd_pre<S, F>(A, g, y, z, lane, P);
+                ilu_bwd_pre<S, F, V>(A, g, y, z, lane, P);
                 if (y + 1 < A.ny) flow_wait(ready + (long long)z * A.ny + y + 1, err);
                 if (z + 1 < A.nz) flow_wait(ready + (long long)(z + 1) * A.ny + y, err);
-                ilu_bwd_fin<S, F>(A, g, y, z, lane, P);
+                ilu_bwd_fin<S, F, V>(A, g, y, z, lane, P);
             }
             flow_signal(ready + (long long)z * A.ny + y);
         }
@@ -481,8 +504,123 @@ static int diag_len(int ny, int nz, int s) {
     return z1 - z0 + 1;
 }
 
+// Column form: warp z owns plane z and walks its lines in sweep order, so the
+// y-neighbour line is its own previous result (kept in registers) and only the
+// z-neighbour comes from another warp (plane z -/+ 1), behind that line's
+// ready flag.  The critical path is about ny line solves plus nz flag hand-offs
+// instead of ny + nz - 1 hand-offs.  Every warp waits only on the warp of the
+// preceding plane, which never waits on it, so with all warps resident
+// (cooperative launch) the sweep cannot deadlock; waits are bounded as above.
+template <int S, typename F, bool FWD, typename V>
+__global__ void __launch_bounds__(256) ilu_col_kernel(IluArgs a0, int *ready, int *err) {
+    using R = typename Compute<F>::type;
+    const IluView<F, V> A(a0);
+    const IluGeo g = ilu_geo(A.nx, A.ny, A.nz);
+    const int lane = threadIdx.x & 31;
+    const int z = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (z >= A.nz) return;
+    int cnt = A.nx - lane * S;
+    cnt = cnt < 0 ? 0 : (cnt > S ? S : cnt);
+    R prev[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) prev[k] = R(0);
+    const unsigned FULL = 0xffffffffu;
+    for (int q = 0; q < A.ny; ++q) {
+        const int y = FWD ? q : A.ny - 1 - q;
+        const long long base = (long long)A.nx * y + g.nxy * z;
+        IluLinePre<S, F> P;
+        if (FWD) ilu_fwd_pre<S, F, V>(A, g, y, z, lane, P);
+        else ilu_bwd_pre<S, F, V>(A, g, y, z, lane, P);
+        if (FWD ? (z > 0) : (z + 1 < A.nz))
+            flow_wait(ready + (long long)(FWD ? z - 1 : z + 1) * A.ny + y, err);
+        R c;
+        if (FWD) {
+            // same arithmetic, in the same order, as ilu_fwd_line
+            R al[S], be[S];
+            R Am = R(1), B = R(0);
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                al[k] = R(1); be[k] = R(0);
+                if (k < cnt) {
+                    const int x = lane * S + k;
+                    const long long a = base + x;
+                    const long long lo = (a < g.M) ? 0 : g.M;
+                    R v = P.rv[k];
+                    if (y > 0 && a - A.nx >= lo) v -= P.cy[k] * prev[k];
+                    if (z > 0 && a - g.nxy >= lo) v -= P.cz[k] * (R)ld_t<true>(A.t + a - g.nxy);
+                    al[k] = (x > 0 && a - 1 >= lo) ? -P.di[k] * P.cx[k] : R(0);
+                    be[k] = P.di[k] * v;
+                }
+                B = fma(al[k], B, be[k]);
+                Am = Am * al[k];
+            }
+#pragma unroll
+            for (int dd = 1; dd < 32; dd <<= 1) {
+                const R Au = __shfl_up_sync(FULL, Am, dd);
+                const R Bu = __shfl_up_sync(FULL, B, dd);
+                if (lane >= dd) { B = fma(Am, Bu, B); Am = Am * Au; }
+            }
+            c = __shfl_up_sync(FULL, B, 1);
+            if (lane == 0) c = R(0);
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                c = fma(al[k], c, be[k]);
+                prev[k] = c;
+                if (k < cnt) A.t[base + lane * S + k] = static_cast<typename std::remove_pointer<decltype(A.t)>::type>(c);
+            }
+        } else {
+            // same arithmetic, in the same order, as ilu_bwd_line
+            R ga[S], de[S];
+            R G = R(1), B = R(0);
+#pragma unroll
+            for (int k = S - 1; k >= 0; --k) {
+                ga[k] = R(1); de[k] = R(0);
+                if (k < cnt) {
+                    const int x = lane * S + k;
+                    const long long a = base + x;
+                    const long long hi = (a < g.M) ? g.M : g.n;
+                    R v = R(0);
+                    if (y + 1 < A.ny && a + A.nx < hi) v += P.cy[k] * prev[k];
+                    if (z + 1 < A.nz && a + g.nxy < hi) v += P.cz[k] * (R)ld_t<true>(A.t + a + g.nxy);
+                    ga[k] = (x + 1 < A.nx && a + 1 < hi) ? -P.di[k] * P.cx[k] : R(0);
+                    de[k] = P.rv[k] - P.di[k] * v;
+                }
+                B = fma(ga[k], B, de[k]);
+                G = G * ga[k];
+            }
+#pragma unroll
+            for (int dd = 1; dd < 32; dd <<= 1) {
+                const R Gd = __shfl_down_sync(FULL, G, dd);
+                const R Bd = __shfl_down_sync(FULL, B, dd);
+                if (lane + dd < 32) { B = fma(G, Bd, B); G = G * Gd; }
+            }
+            c = __shfl_down_sync(FULL, B, 1);
+            if (lane == 31) c = R(0);
+#pragma unroll
+            for (int k = S - 1; k >= 0; --k) {
+                c = fma(ga[k], c, de[k]);
+                prev[k] = c;
+                if (k < cnt) A.t[base + lane * S + k] = static_cast<typename std::remove_pointer<decltype(A.t)>::type>(c);
+            }
+        }
+        flow_signal(ready + (long long)z * A.ny + y);
+    }
+}
+
+// Blocks of a cooperative launch of kernel k with every block resident (0: not possible).
+template <class K>
+static int coop_blocks(K k) {
+    int dev = 0, coop = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 256, 0) != cudaSuccess)
+        return 0;
+    return coop ? per * sms : 0;
+}
+
 // Blocks of a cooperative dataflow launch: every block resident (0: not possible).
-template <int S, typename F, bool FWD>
+template <int S, typename F, bool FWD, typename V = typename Compute<F>::type>
 static int flow_grid() {
     static int cached = -1;
     if (cached < 0) {
@@ -490,7 +628,7 @@ static int flow_grid() {
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ilu_flow_kernel<S, F, FWD>, 256, 0) != cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ilu_flow_kernel<S, F, FWD, V>, 256, 0) != cudaSuccess)
             cached = 0;
         else
             cached = coop ? per * sms : 0;
@@ -541,18 +679,40 @@ static cudaError_t ilu_solve_s(const KernelCtx &c, const double *r, double *t, c
     a.r = r; a.t = t;
     a.ctl = nullptr;
     const int nd = c.ny + c.nz - 1;
+    // the cooperative forms run on r and t in the arithmetic type V (FP32 copies
+    // for FP32/BF16 factors: no conversion on their dependency chain)
+    using V = typename Compute<F>::type;
+    static const int cf = coop_blocks(ilu_col_kernel<S, F, true, V>);
+    static const int cb = coop_blocks(ilu_col_kernel<S, F, false, V>);
+    const int ncol = (c.nz + 7) / 8;
+    const bool col = ncol <= cf && ncol <= cb;
     const int gf = flow_grid<S, F, true>(), gb = flow_grid<S, F, false>();
-    if (c.ws.ilu_ready && gf > 0 && gb > 0) {
-        // dataflow form: two cooperative launches
+    if (c.ws.ilu_ready && (col || (gf > 0 && gb > 0)) && (sizeof(V) == 8 || c.ws.ilu_v)) {
         int *ready = c.ws.ilu_ready, *err = c.ws.flags;
+        cudaError_t e = cudaSuccess;
+        // FP32 copies (FP32/BF16 factors): r -> ilu_v[0, n), t in ilu_v[n, 2n)
+        float *rv = static_cast<float *>(c.ws.ilu_v), *tv = rv ? rv + c.n : nullptr;
+        if constexpr (sizeof(V) == 4) {
+            f64_to_f32_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, r, rv);
+            a.r = rv;
+            a.t = tv;
+            e = cudaGetLastError();
+        }
         void *args[] = {&a, &ready, &err};
         const size_t fb = sizeof(int) * (size_t)c.ny * c.nz;
-        cudaError_t e = cudaMemsetAsync(ready, 0, fb, st);
-        if (e == cudaSuccess)
-            e = cudaLaunchCooperativeKernel((const void *)ilu_flow_kernel<S, F, true>, gf, 256, args, 0, st);
+        const void *kf = col ? (const void *)ilu_col_kernel<S, F, true, V> : (const void *)ilu_flow_kernel<S, F, true, V>;
+        const void *kb = col ? (const void *)ilu_col_kernel<S, F, false, V> : (const void *)ilu_flow_kernel<S, F, false, V>;
+        const int blf = col ? ncol : gf, blb = col ? ncol : gb;
         if (e == cudaSuccess) e = cudaMemsetAsync(ready, 0, fb, st);
-        if (e == cudaSuccess)
-            e = cudaLaunchCooperativeKernel((const void *)ilu_flow_kernel<S, F, false>, gb, 256, args, 0, st);
+        if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(kf, blf, 256, args, 0, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ready, 0, fb, st);
+        if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(kb, blb, 256, args, 0, st);
+        if constexpr (sizeof(V) == 4) {
+            if (e == cudaSuccess) {
+                f32_to_f64_kernel<<<grid_for(c.n), kThreads, 0, st>>>(c.n, tv, t);
+                e = cudaGetLastError();
+            }
+        }
         return e;
     }
     for (int s = 0; s < nd; ++s) {
@@ -583,7 +743,7 @@ static long long ilu_launches_t(const KernelCtx &c) {
 #define FFP_CASE(SS)                                                                          \
     case SS:                                                                                   \
         return (c.ws.ilu_ready && flow_grid<SS, F, true>() > 0 && flow_grid<SS, F, false>() > 0) \
-                   ? 2                                                                         \
+                   ? (sizeof(typename Compute<F>::type) == 4 ? 4 : 2)                           \
                    : 2LL * (c.ny + c.nz - 1);
         FFP_SLOT_LIST(FFP_CASE)
 #undef FFP_CASE

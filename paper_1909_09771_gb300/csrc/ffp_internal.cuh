@@ -576,8 +576,10 @@ struct Ws {
     double *sF[2][2];
     double *sW[2][2];
     double *sC[2][3];
-    // ILU(0) dataflow sweeps: ready flag per line [ny * nz]
+    // ILU(0) dataflow sweeps: ready flag per line [ny * nz]; FP32 copies of r and t
+    // (FP32/BF16 factors: 2 N floats, else null)
     int *ilu_ready;
+    void *ilu_v;
     // reductions
     double *red;   // partial sums [kRedSlots]
     double *scal;  // scalars [kScal]

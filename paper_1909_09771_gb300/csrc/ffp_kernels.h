@@ -124,8 +124,8 @@ long long ilu_solve_launches(const KernelCtx &c);  // kernels one launch_ilu_sol
 struct IluArgs {
     int nx, ny, nz;
     const void *dinv, *lx, *ly, *lz;  // 1/D and the x, y, z bands of A
-    const double *r;
-    double *t;
+    const void *r;                    // right-hand side, FP64 (FP32 in the single-instance
+    void *t;                          // cooperative forms with FP32/BF16 factors); result
     const int *ctl;  // the pair is skipped unless *ctl & 1 (null: always run)
 };
 // ILU(0) solves of every pair of a device table whose lines all use `slots`
