@@ -216,7 +216,7 @@ typedef struct ffp_batch ffp_batch;
 
 /* Launch configuration chosen by ffp_batch_tune.  It never changes a result. */
 typedef struct {
-    int ilu_warps;   /* lines per CTA of the ILU(0) sweeps (1..8) */
+    int ilu_warps;   /* warps per CTA of the ILU(0) sweeps (1..8; each warp walks one plane at a time) */
     int branches;    /* 1: the slot-count groups run as parallel graph branches; 0: in sequence */
     double ms;       /* mean time (ms) of one preconditioner application to every pair
                         under this configuration, as timed by ffp_batch_tune */

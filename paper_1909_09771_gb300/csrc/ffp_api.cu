@@ -85,7 +85,9 @@ size_t ffp::carve_workspace(const ffp_grid *g, int prec, int S_force, char *base
         for (int b = 0; b < 3; ++b) w.sC[h][b] = (double *)take(8 * nxy);
     }
     w.ilu_ready = (int *)take(4 * (size_t)g->ny * g->nz);
-    w.ilu_v = (prec != FFP_FP64) ? take(4 * 2 * n) : nullptr;
+    w.ilu_sync = (int *)take(4 * 32);
+    w.ilu_v = (prec != FFP_FP64) ? take(4 * n) : nullptr;
+    w.ilu_tw = (prec != FFP_FP64) ? (unsigned long long *)take(8 * n) : nullptr;
     w.red = (double *)take(8 * (size_t)kRedSlots);
     // scalar block and flags are contiguous so one copy brings both back
     w.scal = (double *)take(8 * (size_t)kScal + 4 * 16);
@@ -185,6 +187,9 @@ int ffp_setup(const ffp_grid *grid, const double *kappa, const ffp_bc *bc, int f
     carve(grid, precision, (char *)workspace, &c.ws);
 
     cudaError_t e = cudaMemsetAsync(c.ws.scal, 0, kScalBytes, st);
+    // ILU(0) sweep epoch 0 and untagged result words (no tag of a solve is 0)
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.ws.ilu_sync, 0, 4 * 32, st);
+    if (e == cudaSuccess && c.ws.ilu_tw) e = cudaMemsetAsync(c.ws.ilu_tw, 0, 8 * (size_t)c.n, st);
     if (e == cudaSuccess)   // record pads must read as 0
         e = cudaMemsetAsync(c.ws.rec, 0,
                             prec_bytes(precision) * (size_t)c.ny * c.nz * (size_t)rec_len(slots), st);

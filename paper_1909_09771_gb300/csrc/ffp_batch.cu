@@ -13,14 +13,17 @@
 //  * solve: the pairs are kept in groups of equal (apply S, ILU S), longest
 //    level-3 chain first inside a group (the CTA scheduler takes blockIdx.y in
 //    order, so the long chains start first).  One CG iteration of all pairs is
-//    one CUDA graph: a branch per group runs the group's ILU(0) wavefront,
-//    apply phases and vector kernels; the graph is captured once and replayed.
+//    one CUDA graph: a branch per group runs the group's ILU(0) column sweeps
+//    (one launch per sweep over every plane of the group's pairs), apply
+//    phases and vector kernels; the graph is captured once and replayed.
+//    Branches run at stream priorities ranked by the group's longest level-3
+//    chain, so the kernels of the batch's critical path get SM slots first.
 //    Each pair's control word in device memory says whether it iterates this
 //    round, whether its direction restarts, or whether its true residual is
 //    checked; kernels of pairs that do not take part return at once.  After a
 //    replay the host reads every pair's scalar block (one copy) and decides for
 //    each pair exactly as the single-instance driver does.
-//  * tuning: the ILU(0) lines per CTA and whether the groups run as parallel
+//  * tuning: the ILU(0) warps per CTA and whether the groups run as parallel
 //    graph branches or one after another are chosen by timing the
 //    preconditioner graph on the batch itself (ffp_batch_tune); neither changes
 //    any result.
@@ -48,6 +51,8 @@ struct PairArgs {
     const double *b;
     double *x;                        // caller's vectors
     double *r, *z, *p, *q, *c1, *c2;  // CG vectors and B_c temporaries
+    float *r32;                       // B_c with FP32/BF16 factors: FP32 copy of r (ILU(0) input)
+    unsigned long long *tw;           // and the ILU(0) sweeps' tagged result words; else null
     void *ra, *za;                    // apply input and output, line-block layout (lb_pos)
     int S;                            // line slot count of the instance
     double *red, *scal;
@@ -86,6 +91,7 @@ __global__ void __launch_bounds__(kThreads) b_resid(const PairArgs *__restrict__
         const double ba = P.b[a];
         const double ra = ba - stencil(g, a, P.d, P.cx, P.cy, P.cz, P.x);
         P.r[a] = ra;
+        if (P.r32) P.r32[a] = (float)ra;
         acc[0] += ra * ra;
         acc[1] += ba * ba;
     }
@@ -182,6 +188,7 @@ __global__ void __launch_bounds__(kThreads) b_update_xr(const PairArgs *__restri
         P.x[a] += alpha * P.p[a];
         const double ra = P.r[a] - alpha * P.q[a];
         P.r[a] = ra;
+        if (P.r32) P.r32[a] = (float)ra;
         acc[0] += ra * ra;
     }
     block_sum<1>(acc, P.red);
@@ -204,25 +211,33 @@ bool grid_ok(const ffp_grid &g) {
 }
 
 // vectors of a pair beyond an instance's first: r z p q c1 c2, the apply input and output
-// blocks, apply scratch (line-block layout), partials
+// blocks, apply scratch (line-block layout), partials, and with FP32/BF16 factors the
+// FP32 copy of the ILU(0) input and the tagged words of its result
 size_t extra_pair_bytes(const ffp_grid &g, int prec) {
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     const size_t ab = (prec == FFP_FP64) ? 8 : 4, lb = (size_t)lb_len(slots_for(g.nx));
     return 6 * al256(8 * n) + 2 * al256(ab * (size_t)g.ny * g.nz * lb) + al256(ab * 2 * (size_t)g.ny * lb) +
-           al256(8 * (size_t)kRedSlots);
+           al256(8 * (size_t)kRedSlots) + (prec == FFP_FP64 ? 0 : al256(4 * n) + al256(8 * n));
 }
+
+// ints of the ILU(0) sync region: per group 2 ticket counters (padded to 32 ints)
+// and one ready flag per line of each of its pairs
+constexpr int kSyncHead = 32;
 
 struct Group {
     int p0, np;  // device pair range
     int S, Si;   // apply and ILU(0) slot counts
-    int nx_max, nb_max, ndiag, maxlines;
+    int nx_max, nb_max;
+    int nitems;        // ILU(0) work items (planes) of the group's pairs
+    long long chain;   // longest level-3 chain of its pairs, (ny + 1)(nz + 1) line solves
+    int *sync;         // the group's ILU(0) sync region
+    size_t sync_bytes;
 };
 
 long long kernel_count_of(const std::vector<Group> &gs, int combo, int f32) {
     long long k = 0;
     for (const Group &g : gs)
-        k += (combo ? 2LL * g.ndiag : 0) + 2 + 3 + 7;
-    (void)f32;
+        k += (combo ? (f32 ? 3 : 2) : 0) + 2 + 3 + 7;
     return k;
 }
 
@@ -241,6 +256,7 @@ struct ffp_batch {
     IluArgs *dilu;
     SetupArgs *dsetup;
     IluPivArgs *dpiv;
+    int *dsync;                    // ILU(0) sync regions of all groups
     int *dctl;
     char *dscal;                   // scalar blocks of all pairs, contiguous
     int *hctl;                     // pinned
@@ -273,10 +289,14 @@ size_t batch_layout(int count, const ffp_grid *grids, int nrhs, int prec, char *
     char *t_setup = take(sizeof(SetupArgs) * count);
     char *t_piv = take(sizeof(IluPivArgs) * count);
     char *t_ctl = take(4 * (size_t)np);
+    size_t sync_ints = 0;
+    for (int i = 0; i < count; ++i) sync_ints += (size_t)nrhs * ((size_t)grids[i].ny * grids[i].nz + kSyncHead);
+    char *t_sync = take(4 * sync_ints);
     char *t_scal = take(kPairScal * np);
     if (B) {
         B->dpairs = (PairArgs *)t_pairs; B->dapply = (ApplyArgs *)t_apply; B->dilu = (IluArgs *)t_ilu;
         B->dsetup = (SetupArgs *)t_setup; B->dpiv = (IluPivArgs *)t_piv; B->dctl = (int *)t_ctl;
+        B->dsync = (int *)t_sync;
         B->dscal = t_scal;
     }
     for (int i = 0; i < count; ++i) {
@@ -294,6 +314,8 @@ size_t batch_layout(int count, const ffp_grid *grids, int nrhs, int prec, char *
                     PairArgs &P = B->pairs[up];
                     P.r = w.r; P.z = w.z; P.p = w.p; P.q = w.q; P.c1 = w.c1; P.c2 = w.c2;
                     P.ra = w.ra; P.za = w.za; P.red = w.red;
+                    P.r32 = (float *)w.ilu_v;
+                    P.tw = w.ilu_tw;
                     (*ascr)[up] = w.ascr;
                 }
                 continue;
@@ -309,6 +331,10 @@ size_t batch_layout(int count, const ffp_grid *grids, int nrhs, int prec, char *
                 P.za = sub(ab * (size_t)g.ny * g.nz * lb);
                 (*ascr)[up] = sub(ab * 2 * (size_t)g.ny * lb);
                 P.red = (double *)sub(8 * (size_t)kRedSlots);
+                if (prec != FFP_FP64) {
+                    P.r32 = (float *)sub(4 * n);
+                    P.tw = (unsigned long long *)sub(8 * n);
+                }
             }
         }
     }
@@ -325,7 +351,8 @@ cudaError_t group_precond(const ffp_batch *B, const Group &g, cudaStream_t s) {
     const dim3 gv(g.nb_max, g.np);
     cudaError_t e = cudaSuccess;
     if (combo)
-        e = launch_ilu_table(B->prec, g.Si, B->dilu + g.p0, g.np, g.ndiag, g.maxlines, B->cfg.ilu_warps, s);
+        e = launch_ilu_table(B->prec, g.Si, B->dilu + g.p0, g.np, g.nitems, g.sync, g.sync_bytes,
+                             B->cfg.ilu_warps, s);
     if (e == cudaSuccess) {
         if (f32) b_prec_in<float><<<gv, kThreads, 0, s>>>(T, combo);
         else b_prec_in<double><<<gv, kThreads, 0, s>>>(T, combo);
@@ -388,7 +415,8 @@ cudaError_t capture(cudaStream_t st, cudaGraphExec_t *out, Fn fn) {
         return e2;
     }
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(out, g, 0);
+    // kernel nodes keep the priority of the stream they were captured from
+    e = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     return e;
 }
@@ -644,6 +672,10 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
         P.scal = reinterpret_cast<double *>(B->dscal + kPairScal * k);
         P.flags = reinterpret_cast<int *>(P.scal + kScal);
         P.ctl = B->dctl + k;
+        if (precond != FFP_PRECOND_COMBO || precision == FFP_FP64) {
+            P.r32 = nullptr;
+            P.tw = nullptr;
+        }
         pt[k] = P;
         ApplyArgs &A = at[k];
         A.nx = c.nx; A.ny = c.ny; A.nz = c.nz;
@@ -654,28 +686,45 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
         A.flags = P.flags;
         A.ctl = P.ctl;
         IluArgs &L = it[k];
+        std::memset(&L, 0, sizeof(L));
         L.nx = c.nx; L.ny = c.ny; L.nz = c.nz;
         L.dinv = c.ws.dinv; L.lx = c.ws.lx; L.ly = c.ws.ly; L.lz = c.ws.l3;
-        L.r = P.r; L.t = P.c1;
+        if (P.r32) {  // FP32 sweeps on tagged words; the backward sweep also stores c1 in FP64
+            L.r = P.r32; L.t = nullptr; L.tw = P.tw; L.out64 = P.c1;
+        } else {
+            L.r = P.r; L.t = P.c1;
+        }
         L.ctl = P.ctl;
+        L.err = P.flags;
         B->nb_max = std::max(B->nb_max, P.nb);
     }
     B->pairs = pt;
+    // groups; each gets its ILU(0) sync region: counters, then its pairs' ready flags
+    int *sync = B->dsync;
     for (int k0 = 0; k0 < B->npairs;) {
         Group g;
         g.p0 = k0;
         g.S = key(ord[k0]).first;
         g.Si = key(ord[k0]).second;
-        g.nx_max = 1; g.nb_max = 1; g.ndiag = 1; g.maxlines = 1;
+        g.nx_max = 1; g.nb_max = 1; g.nitems = 0; g.chain = 0;
+        g.sync = sync;
+        int *ready = sync + kSyncHead;
         int k1 = k0;
         while (k1 < B->npairs && key(ord[k1]) == key(ord[k0])) {
+            IluArgs &L = it[k1];
             const PairArgs &P = pt[k1++];
             g.nx_max = std::max(g.nx_max, P.nx);
             g.nb_max = std::max(g.nb_max, P.nb);
-            g.ndiag = std::max(g.ndiag, P.ny + P.nz - 1);
-            g.maxlines = std::max(g.maxlines, std::min(P.ny, P.nz));
+            g.chain = std::max(g.chain, (long long)(P.ny + 1) * (P.nz + 1));
+            L.item0 = g.nitems;
+            L.ready = ready;
+            L.sync = sync;
+            g.nitems += P.nz;
+            ready += (size_t)P.ny * P.nz;
         }
         g.np = k1 - k0;
+        g.sync_bytes = 4 * (size_t)(ready - sync);
+        sync = ready;
         B->groups.push_back(g);
         k0 = k1;
     }
@@ -685,11 +734,14 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->dilu, it.data(), sizeof(IluArgs) * B->npairs, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->dctl, 0, 4 * (size_t)B->npairs, st);
-    // padding positions of the apply input blocks must read 0; b_prec_in writes only cells
+    // padding positions of the apply input blocks must read 0; b_prec_in writes only cells;
+    // ILU(0) epochs start at 0 and the tagged words untagged
     for (int k = 0; k < B->npairs && e == cudaSuccess; ++k) {
         const PairArgs &P = pt[k];
         e = cudaMemsetAsync(P.ra, 0, (precision == FFP_FP64 ? 8 : 4) * (size_t)P.ny * P.nz * lb_len(P.S), st);
+        if (e == cudaSuccess && P.tw) e = cudaMemsetAsync(P.tw, 0, 8 * (size_t)P.n, st);
     }
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->dsync, 0, 4 * (size_t)(sync - B->dsync), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     // ---- streams and events of the graphs
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->gs, cudaStreamNonBlocking);
@@ -697,8 +749,20 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreate(&B->tev[k]);
     B->side.assign(B->groups.size(), nullptr);
     B->join.assign(B->groups.size(), nullptr);
+    // branch priorities: the group with the longest level-3 chain highest, so its
+    // kernels (the batch's critical path) get SM slots first
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    std::vector<int> rank(B->groups.size());
+    for (size_t k = 0; k < B->groups.size(); ++k) {
+        int r = 0;
+        for (size_t j = 0; j < B->groups.size(); ++j)
+            if (B->groups[j].chain > B->groups[k].chain || (B->groups[j].chain == B->groups[k].chain && j < k)) ++r;
+        rank[k] = r;
+    }
     for (size_t k = 0; k < B->groups.size() && e == cudaSuccess; ++k) {
-        e = cudaStreamCreateWithFlags(&B->side[k], cudaStreamNonBlocking);
+        const int prio = std::min(least, greatest + rank[k]);  // greatest is the numerically smallest
+        e = cudaStreamCreateWithPriority(&B->side[k], cudaStreamNonBlocking, prio);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->join[k], cudaEventDisableTiming);
     }
     if (e != cudaSuccess) return fail(FFP_ERR_CUDA);
@@ -768,14 +832,17 @@ int ffp_batch_tune(ffp_batch *B, const char *cache_path, ffp_batch_config *out, 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(B->gs, ev, 0);
     // every pair takes part; the preconditioner reads r, set to zero here
     for (int k = 0; k < B->npairs; ++k) B->hctl[k] = CTL_ITER;
-    for (int k = 0; k < B->npairs && e == cudaSuccess; ++k)
+    for (int k = 0; k < B->npairs && e == cudaSuccess; ++k) {
         e = cudaMemsetAsync(B->pairs[k].r, 0, 8 * (size_t)B->pairs[k].n, B->gs);
+        if (e == cudaSuccess && B->pairs[k].r32)
+            e = cudaMemsetAsync(B->pairs[k].r32, 0, 4 * (size_t)B->pairs[k].n, B->gs);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->dctl, B->hctl, 4 * (size_t)B->npairs, cudaMemcpyHostToDevice, B->gs);
     const bool combo = B->precond == FFP_PRECOND_COMBO;
     std::vector<ffp_batch_config> cand;
     for (int br = 0; br <= 1; ++br)
-        for (int w : {2, 4, 8}) {
+        for (int w : {1, 2, 4, 8}) {
             if (!combo && w != 4) continue;
             ffp_batch_config c;
             c.ilu_warps = w; c.branches = br; c.ms = 0.0; c.ntd_ms = 0.0; c.from_cache = 0;

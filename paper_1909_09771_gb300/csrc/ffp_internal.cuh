@@ -576,10 +576,14 @@ struct Ws {
     double *sF[2][2];
     double *sW[2][2];
     double *sC[2][3];
-    // ILU(0) dataflow sweeps: ready flag per line [ny * nz]; FP32 copies of r and t
-    // (FP32/BF16 factors: 2 N floats, else null)
+    // ILU(0) sweeps: ready flag per line [ny * nz] (flagged forms); sync head [32]
+    // (ticket counters, sweep epoch); with FP32/BF16 factors the FP32 copy of r [N]
+    // and the tagged result words [N] (FP32 value + sweep tag; the dataflow form
+    // keeps its FP32 t there), else null
     int *ilu_ready;
+    int *ilu_sync;
     void *ilu_v;
+    unsigned long long *ilu_tw;
     // reductions
     double *red;   // partial sums [kRedSlots]
     double *scal;  // scalars [kScal]

@@ -124,14 +124,26 @@ long long ilu_solve_launches(const KernelCtx &c);  // kernels one launch_ilu_sol
 struct IluArgs {
     int nx, ny, nz;
     const void *dinv, *lx, *ly, *lz;  // 1/D and the x, y, z bands of A
-    const void *r;                    // right-hand side, FP64 (FP32 in the single-instance
-    void *t;                          // cooperative forms with FP32/BF16 factors); result
-    const int *ctl;  // the pair is skipped unless *ctl & 1 (null: always run)
+    const void *r;                    // right-hand side, FP64 (FP32 in the column and
+    void *t;                          // dataflow forms with FP32/BF16 factors); result
+    double *out64;   // column forms, backward sweep: the result also stored here in FP64 (or null)
+    const int *ctl;  // table form: the pair is skipped unless *ctl & 1 (null: always run)
+    int *ready;      // table form: the pair's ny*nz line ready flags (FP64 values)
+    int *err;        // table form: the pair's flags (FL_TIMEOUT)
+    unsigned long long *tw;  // column forms with FP32 values: tagged result words [N]
+                             // (zeroed at setup), used in place of t
+    int *sync;       // column forms with FP32 values: sync head (sync[2] = sweep epoch)
+    int item0;       // table form: the pair's first work item (plane)
 };
-// ILU(0) solves of every pair of a device table whose lines all use `slots`
-// (ndiag, maxlines: the largest wavefront length and diagonal of the pairs;
-// warps: lines per CTA)
-cudaError_t launch_ilu_table(int prec, int slots, const IluArgs *table, int npairs, int ndiag,
-                             int maxlines, int warps, cudaStream_t st);
+// ILU(0) solves of every pair of a device table whose lines all use `slots`,
+// as ticketed column sweeps (one work item = one plane; entry k's items start
+// at item0, nitems in all).  sync: sync_bytes of device memory; sync[0],
+// sync[1] are the two sweeps' ticket counters and sync[2] the sweep epoch
+// (zeroed at setup; FP32 values: every entry's `sync` is this pointer),
+// followed by the entries' ready flags (FP64 values).  Before the sweeps the
+// counters are reset and the epoch advanced (FP32 values) or the whole region
+// zeroed (FP64 values).  warps: warps per CTA (1..8); one warp per item.
+cudaError_t launch_ilu_table(int prec, int slots, const IluArgs *table, int npairs, int nitems, int *sync,
+                             size_t sync_bytes, int warps, cudaStream_t st);
 
 }  // namespace ffp

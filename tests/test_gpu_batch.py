@@ -5,7 +5,7 @@ A batched pair runs the same kernels, line slot count, reduction partition and
 control flow as its standalone ffp_pcg_solve, so its iteration count must be
 equal and its solution equal to 1e-12 relative (the only allowed difference is
 none at all in practice; the bound leaves room for nothing but rounding).  The
-launch configuration (ILU(0) lines per CTA, parallel or sequential groups) must
+launch configuration (ILU(0) warps per CTA, parallel or sequential groups) must
 not change any result.  One pair is also checked against the FP64 oracle's PCG
 with the PCG tolerances of the single-instance tests (iterations +-1, solution
 1e-7), and the full 64-instance workload is checked by independent true

@@ -173,6 +173,24 @@ def test_combination_parity_fp32(grid):
     assert relerr(host(P.apply(dev(r))), zr) <= 1e-5
 
 
+@pytest.mark.parametrize("grid", [(33, 1, 7), (40, 6, 1), (350, 3, 4), (70, 24, 20)])
+def test_combination_parity_fp32_shapes(grid):
+    """B_c with FP32 factors on degenerate and many-plane shapes (ny = 1, nz = 1,
+    the longest line, several CTAs of plane sweeps): within FP32 rounding of the
+    FP64 oracle, and repeated applies (each a new ILU(0) sweep epoch) are bitwise
+    identical."""
+    w = I.random_small(grid, 35, contrast_exp=3)
+    P = ffp.Preconditioner(grid, dev(w["kappa"]), w["bc"], "fp32", precond="combo")
+    bands = o.assemble(grid, w["kappa"], w["bc"])
+    r = np.random.default_rng(36).standard_normal(int(np.prod(grid)))
+    zr = o.combo_apply(grid, bands, o.setup(grid, bands), o.ilu0_setup(grid, bands), r)
+    rd = dev(r)
+    z1 = P.apply(rd)
+    assert relerr(host(z1), zr) <= 1e-5
+    for _ in range(3):
+        assert torch.equal(P.apply(rd), z1)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_combination_pcg_blocks32(precision):
     w = I.workload_blocks32(seed=0)
