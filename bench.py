@@ -181,11 +181,16 @@ def run_ours(args):
         net = LF.load_weights(args.weights, device=dev)
         t_buf = torch.empty(n, dtype=torch.float64, device=dev)
 
-    def step(kap, rhs, xout):
+    def step(kap, rhs, xout, marks=None):
         # learned filter: the network's inference on this kappa is part of the step
+        if marks is not None:
+            marks.append([torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)])
+            marks[-1][0].record(stream)
         t = net.forward(grid, kap, batch=1, t=t_buf) if net is not None else None
         P = ffp.Preconditioner(grid, kap, bc, args.precision, precond=args.precond,
                                workspace=work, t=t)
+        if marks is not None:
+            marks[-1][1].record(stream)
         xout.zero_()
         _, st = P.solve(rhs, x=xout, rtol=RTOL, maxit=MAXIT, check=False)
         P.close()
@@ -201,16 +206,18 @@ def run_ours(args):
     # ---- device-resident timed region
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
+    marks = []  # CUDA events around each step's setup (filter inference included)
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            stats.append(step(kappa, b, x))
+            stats.append(step(kappa, b, x, marks))
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
+    setup_ms = sum(m0.elapsed_time(m1) for m0, m1 in marks) / len(marks)
     # ---- end to end through the public API with host buffers
     e2 = []
     barrier()
@@ -257,6 +264,7 @@ def run_ours(args):
             "filter": args.filter if args.filter == "rowsum" else
             "learned (conv net on log10 kappa, weights " + os.path.basename(args.weights) + ")",
             "rtol": RTOL,
+            "setup_ms": setup_ms,
             "iters": st["iters"],
             "rel_res_true": st["rel_res_true"],
             "converged": ok,
