@@ -132,10 +132,7 @@ __global__ void __launch_bounds__(128) ilu_pivot_kernel(IluPivArgs P0,
     }
     double pp = __shfl_up_sync(FULL, p11, 1), qq = __shfl_up_sync(FULL, p21, 1);
     if (lane == 0) { pp = 1.0; qq = 0.0; }
-    {
-        const double mx = fmax(fabs(pp), fabs(qq));
-        if (mx > 0.0 && isfinite(mx)) { const int e = ilogb(mx); pp = scalbn(pp, -e); qq = scalbn(qq, -e); }
-    }
+    scale2(pp, qq);
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < S; ++k)

@@ -312,12 +312,49 @@ __device__ __forceinline__ void twisted_solve_pre(const R (&al)[S], const R (&ga
 // powers of two, which leaves p/q unchanged) and then substituted slot by
 // slot from the lane's incoming (p, q).  FP64.  Returns 1/M per slot and for
 // the twist cell; `bad` is set if a pivot is not positive and finite.
-__device__ __forceinline__ void scale4(double &a, double &b, double &c, double &d) {
-    const double mx = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(c), fabs(d)));
-    if (mx > 0.0 && isfinite(mx)) {
-        const int e = ilogb(mx);
-        a = scalbn(a, -e); b = scalbn(b, -e); c = scalbn(c, -e); d = scalbn(d, -e);
+//
+// The scale is 2^-e, e the binary exponent of the largest magnitude.  It is
+// read from the IEEE-754 bit patterns with integer operations, so that only
+// the exact multiplies by 2^-e use the FP64 pipe (a scarce unit on this GPU);
+// the result is that of ilogb/scalbn.  Values that are all zero or not all
+// finite are left as they are; the rare case of a largest magnitude that is
+// subnormal, or too large for 2^-e to be a normal number, takes ilogb/scalbn.
+__device__ __forceinline__ int biased_exp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+template <int N>
+__device__ __forceinline__ void scale_pow2(double (&v)[N]) {
+    int em = 0;
+    bool nonzero = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        em = max(em, biased_exp(v[i]));
+        nonzero |= (__double2hiint(v[i]) & 0x7fffffff) != 0 || __double2loint(v[i]) != 0;
     }
+    if (em == 0x7ff || !nonzero) return;  // a value is not finite, or all are zero
+    if (em >= 1 && em <= 2045) {
+        const double f = __hiloint2double((2046 - em) << 20, 0);  // 2^-(em - 1023)
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] *= f;
+        return;
+    }
+    double mx = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) mx = fmax(mx, fabs(v[i]));
+    const int e = ilogb(mx);
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = scalbn(v[i], -e);
+}
+
+__device__ __forceinline__ void scale4(double &a, double &b, double &c, double &d) {
+    double v[4] = {a, b, c, d};
+    scale_pow2<4>(v);
+    a = v[0]; b = v[1]; c = v[2]; d = v[3];
+}
+
+__device__ __forceinline__ void scale2(double &a, double &b) {
+    double v[2] = {a, b};
+    scale_pow2<2>(v);
+    a = v[0]; b = v[1];
 }
 
 template <int S>
@@ -359,10 +396,7 @@ __device__ __forceinline__ void twisted_pivots(int cnt, int lane, const double (
     double pp = __shfl_up_sync(FULL, p11, 1, 16);
     double qq = __shfl_up_sync(FULL, p21, 1, 16);
     if (j == 0) { pp = 1.0; qq = 0.0; }
-    {
-        const double mx = fmax(fabs(pp), fabs(qq));
-        if (mx > 0.0 && isfinite(mx)) { const int e = ilogb(mx); pp = scalbn(pp, -e); qq = scalbn(qq, -e); }
-    }
+    scale2(pp, qq);
     bool b_ = false;
 #pragma unroll
     for (int s = 0; s < S; ++s) {

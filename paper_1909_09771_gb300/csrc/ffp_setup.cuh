@@ -79,7 +79,8 @@ __device__ __forceinline__ void line_schur(const LineMap &L, int nx, int lane, i
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         if (s < cnt) {
-            be[s] = (fabs(w[s]) < 1e-300) ? 1.0 / st.Td[s] : v[s] / w[s];
+            const bool z = fabs(w[s]) < 1e-300;   // one divide either way
+            be[s] = (z ? 1.0 : v[s]) / (z ? st.Td[s] : w[s]);
             const int a = slot_cell<S>(L, lane, s);
             SB[a] = be[s];
             SP[a] = pa[s];
@@ -87,7 +88,10 @@ __device__ __forceinline__ void line_schur(const LineMap &L, int nx, int lane, i
             be[s] = 0.0;
         }
     }
-    bem = (fabs(wm) < 1e-300) ? 1.0 / st.Tdm : vm / wm;
+    {
+        const bool z = fabs(wm) < 1e-300;
+        bem = (z ? 1.0 : vm) / (z ? st.Tdm : wm);
+    }
     if (lane == 0) { SB[L.m] = bem; SP[L.m] = pm; }
     __syncwarp();
 #pragma unroll
@@ -316,8 +320,10 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
                                                       cnt);
             }
             __syncthreads();
-            for (long e = tid; e < nxy; e += blockDim.x)
-                V[e] = (fabs(W[e]) < 1e-300) ? 1.0 / Pd[e] : V[e] / W[e];
+            for (long e = tid; e < nxy; e += blockDim.x) {
+                const bool z = fabs(W[e]) < 1e-300;  // one divide either way
+                V[e] = (z ? 1.0 : V[e]) / (z ? Pd[e] : W[e]);
+            }
             __syncthreads();
             const bool to_mid = (dst == mz);
             double *od = to_mid ? A.ws.sC[h][0] : A.ws.sP[h][(t + 1) & 1][0];
