@@ -84,6 +84,9 @@ typedef struct {
                              of each apply, precision conversions excluded */
     int napply;           /* number of preconditioner applies */
     long long launches;   /* kernels this call launched */
+    int iters_rec;        /* first iteration at which the recursive ||r|| / ||b|| fell below rtol
+                             (-1 if it never did); iters can be larger when the true residual,
+                             checked then, was not yet below rtol and the solve went on */
 } ffp_stats;
 
 typedef struct ffp_handle ffp_handle;

@@ -252,7 +252,7 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
     const KernelCtx &c = h->c;
     const int flexible = (c.prec != FFP_FP64) || (c.precond == FFP_PRECOND_COMBO);
     auto t0 = std::chrono::steady_clock::now();
-    int it = 0, fresh = 1, status = FFP_OK;
+    int it = 0, fresh = 1, status = FFP_OK, it_rec = -1;
     double bb = 0.0, rr = 0.0;
     double pre_ms = 0.0, ntd_ms = 0.0;
     long long nl = 0;
@@ -279,6 +279,7 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
     }
     for (;;) {
         if (std::sqrt(rr / bb) < rtol) {
+            if (it_rec < 0) it_rec = it;
             // confirm with the true residual; continue from it if it is not converged
             FFP_TRY(launch_resid(c, b, x, st));
             FFP_TRY(launch_finalize(c, FIN_RESID, 0, flexible, st));
@@ -329,6 +330,7 @@ done:
             nl += 2;
         }
         stats->launches = nl;
+        stats->iters_rec = it_rec;
         stats->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return status;

@@ -928,7 +928,7 @@ int ffp_batch_solve(ffp_batch *B, const double *const *b, double *const *x, doub
     int status = cuda_status(e);
     long long launches = 0;
     std::vector<double> bb(np, 0.0), rr(np, 0.0);
-    std::vector<int> it(np, 0), fresh(np, 1), done(np, 0), st_p(np, FFP_OK);
+    std::vector<int> it(np, 0), fresh(np, 1), done(np, 0), st_p(np, FFP_OK), it_rec(np, -1);
     auto run = [&](cudaGraphExec_t g, long long nk) {
         launches += nk;
         return cudaGraphLaunch(g, gs) == cudaSuccess && cudaStreamSynchronize(gs) == cudaSuccess;
@@ -954,6 +954,7 @@ int ffp_batch_solve(ffp_batch *B, const double *const *b, double *const *x, doub
         for (int k = 0; k < np; ++k) {
             B->hctl[k] = 0;
             if (!done[k] && std::sqrt(rr[k] / bb[k]) < rtol) {
+                if (it_rec[k] < 0) it_rec[k] = it[k];
                 B->hctl[k] = CTL_RESID;
                 check = true;
             }
@@ -1010,6 +1011,7 @@ int ffp_batch_solve(ffp_batch *B, const double *const *b, double *const *x, doub
         s.solve_s = secs;
         s.napply = it[k];
         s.launches = launches;
+        s.iters_rec = (bb[k] == 0.0) ? 0 : it_rec[k];
     }
     if (cudaEventRecord(ev, gs) == cudaSuccess) cudaStreamWaitEvent(st, ev, 0);
     cudaEventDestroy(ev);

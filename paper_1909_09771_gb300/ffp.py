@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("rel_res_true", ctypes.c_double), ("solve_s", ctypes.c_double),
                 ("precond_ms", ctypes.c_double), ("ntd_ms", ctypes.c_double),
-                ("napply", ctypes.c_int), ("launches", ctypes.c_longlong)]
+                ("napply", ctypes.c_int), ("launches", ctypes.c_longlong), ("iters_rec", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

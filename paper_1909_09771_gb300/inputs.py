@@ -18,6 +18,10 @@ x and y faces, unless stated):
   batched      64 instances, each nx,ny,nz uniform in [48, 160], kappa = 10^e on
                an 8x8x8 block partition, 4 right-hand sides N(0,1) each
   grf_train    64^3 GRF instances with contrast 10^4 (kappa = 10^(2 g))
+  paper<T>_<n> the paper's own test problems (Sec. IV, "Test Matrices"): n^3,
+               Dirichlet u=0 on all six faces, kappa of type T = 1 (skyscrapers
+               with checkerboard jumps), 2 (a ring of kappa 1e3), 3 (Poisson);
+               b = h^3 (f = 1 scaled by cell volume; the paper does not state f)
 """
 from __future__ import annotations
 
@@ -108,6 +112,39 @@ def workload_layered128(seed=0, n=128):
     h = 1.0 / n
     b = np.full(n ** 3, h ** 3)
     return dict(name=f"layered{n}", grid=grid, kappa=kappa, bc=BC_Z_DIRICHLET, b=b)
+
+
+def kappa_paper(kind, n):
+    """Coefficient of the paper's test matrix type `kind` (Sec. IV, "Test
+    Matrices") at the cell centres x = ((i+1/2)/n, (j+1/2)/n, (k+1/2)/n) of
+    an n^3 unit cube, x fastest:
+      1: 10^3 ([10 x_2] + 1) where [10 x_i] is even for i = 1, 2, 3, else 1
+         ([.] the integer part, x_2 the y coordinate);
+      2: 10^3 on the shell 1/(2 sqrt 2) <= |x - c| <= 1/2, c the cube centre,
+         else 1;
+      3: 1."""
+    c = (np.arange(n) + 0.5) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")  # arrays [z, y, x]: x fastest when raveled
+    if kind == 1:
+        fx, fy, fz = np.floor(10 * x), np.floor(10 * y), np.floor(10 * z)
+        even = (fx % 2 == 0) & (fy % 2 == 0) & (fz % 2 == 0)
+        k = np.where(even, 1e3 * (fy + 1.0), 1.0)
+    elif kind == 2:
+        r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
+        k = np.where((r >= 1.0 / (2.0 * np.sqrt(2.0))) & (r <= 0.5), 1e3, 1.0)
+    elif kind == 3:
+        k = np.ones((n, n, n))
+    else:
+        raise ValueError(kind)
+    return np.ascontiguousarray(k, dtype=np.float64).ravel()
+
+
+def workload_paper(kind, n):
+    """The paper's test problem of type `kind` on n^3 (Sec. IV): all faces
+    Dirichlet, b = h^3 (f = 1)."""
+    h = 1.0 / n
+    return dict(name=f"paper{kind}_{n}", grid=(n, n, n), kappa=kappa_paper(kind, n),
+                bc=BC_ALL_DIRICHLET, b=np.full(n ** 3, h ** 3))
 
 
 def workload_grf(seed=0, n=350, exponent=3.0):
