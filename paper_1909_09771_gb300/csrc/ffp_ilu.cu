@@ -8,11 +8,18 @@
 // and B_ILU0 = (D + L) D^{-1} (D + U).
 //
 // GPU schedule: line (y, z) of the grid depends only on lines (y-1, z) and
-// (y, z-1), so all lines on a diagonal y + z = s are independent; each launch
-// handles one diagonal, one warp per line.  Along a line the recurrence in x
-// is first order: an affine map per cell (triangular sweeps) or a Moebius map
-// (pivots), evaluated as lane-local composition + a 32-lane scan + lane-local
-// substitution, lane l holding cells l*S .. l*S+S-1.
+// (y, z-1).  Along a line the recurrence in x is first order: an affine map
+// per cell (triangular sweeps) or a Moebius map (pivots), evaluated as
+// lane-local composition + a 32-lane scan + lane-local substitution, lane l
+// holding cells l*S .. l*S+S-1.  Three schedules of the sweeps, same
+// arithmetic in the same order:
+//  * column form (used whenever it fits): the warp of plane z walks its lines
+//    in order and takes the z-neighbour line from the warp of plane z -/+ 1;
+//    one cooperative launch per sweep for a single instance, one ticketed
+//    launch per sweep over all planes of a batch group;
+//  * dataflow form: lines in diagonal order over all warps, ready flags;
+//  * wavefront form: one launch per diagonal y + z = s, one warp per line
+//    (the pivots always use it; the sweeps only as a last resort).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
