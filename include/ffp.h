@@ -36,7 +36,8 @@ extern "C" {
 #define FFP_ERR_CUDA (-2)           /* a CUDA runtime call failed */
 #define FFP_ERR_BREAKDOWN (-3)      /* a non-positive / non-finite pivot or diagonal in setup,
                                        or (p, Ap) <= 0 in CG */
-#define FFP_ERR_NOT_CONVERGED (-4)  /* maxit reached; x holds the last iterate */
+#define FFP_ERR_NOT_CONVERGED (-4)  /* maxit reached, or the true residual stopped falling;
+                                       x holds the last iterate */
 #define FFP_ERR_TIMEOUT (-5)        /* a bounded wait inside a kernel gave up (results unusable) */
 #define FFP_ERR_UNSUPPORTED (-6)    /* the requested option is not available */
 
@@ -151,7 +152,9 @@ int ffp_apply(ffp_handle *h, const double *r, double *z, void *stream);
  *   b      device FP64 [N]
  *   x      device FP64 [N]: in x0, out the solution (b = 0 gives x = 0, 0 iterations)
  *   stats  host pointer or NULL
- * Returns FFP_ERR_NOT_CONVERGED at maxit, FFP_ERR_BREAKDOWN if (p, A p) <= 0. */
+ * Returns FFP_ERR_NOT_CONVERGED at maxit, or when three confirmations in a row
+ * fail to halve the best true residual (rtol below what an FP64 iterate can
+ * reach, about eps |A||x| / |b|); FFP_ERR_BREAKDOWN if (p, A p) <= 0. */
 int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int maxit,
                   ffp_stats *stats, void *stream);
 

@@ -253,6 +253,10 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
     const int flexible = (c.prec != FFP_FP64) || (c.precond == FFP_PRECOND_COMBO);
     auto t0 = std::chrono::steady_clock::now();
     int it = 0, fresh = 1, status = FFP_OK, it_rec = -1;
+    // true residuals at confirmations: the best so far and the confirmations in a row
+    // that did not halve it (the true residual has reached its FP64 floor)
+    double best_true = -1.0;
+    int stalls = 0;
     double bb = 0.0, rr = 0.0;
     double pre_ms = 0.0, ntd_ms = 0.0;
     long long nl = 0;
@@ -287,6 +291,9 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
             if ((status = read_scalars(h, st)) != FFP_OK) goto done;
             rr = h->host_scal[SC_RR];
             if (std::sqrt(rr / bb) < rtol) break;
+            stalls = (best_true >= 0.0 && rr > 0.25 * best_true) ? stalls + 1 : 0;
+            if (best_true < 0.0 || rr < best_true) best_true = rr;
+            if (stalls >= kStallConfirms) { status = FFP_ERR_NOT_CONVERGED; break; }
             fresh = 1;
         }
         if (it >= maxit) { status = FFP_ERR_NOT_CONVERGED; break; }

@@ -929,6 +929,8 @@ int ffp_batch_solve(ffp_batch *B, const double *const *b, double *const *x, doub
     long long launches = 0;
     std::vector<double> bb(np, 0.0), rr(np, 0.0);
     std::vector<int> it(np, 0), fresh(np, 1), done(np, 0), st_p(np, FFP_OK), it_rec(np, -1);
+    std::vector<int> stalls(np, 0);           // as in the single-instance driver
+    std::vector<double> best_true(np, -1.0);
     auto run = [&](cudaGraphExec_t g, long long nk) {
         launches += nk;
         return cudaGraphLaunch(g, gs) == cudaSuccess && cudaStreamSynchronize(gs) == cudaSuccess;
@@ -964,8 +966,18 @@ int ffp_batch_solve(ffp_batch *B, const double *const *b, double *const *x, doub
             for (int k = 0; k < np; ++k)
                 if (B->hctl[k] & CTL_RESID) {
                     rr[k] = pscal(B, k)[SC_RR];
-                    if (std::sqrt(rr[k] / bb[k]) < rtol) done[k] = 1;
-                    else fresh[k] = 1;
+                    if (std::sqrt(rr[k] / bb[k]) < rtol) {
+                        done[k] = 1;
+                        continue;
+                    }
+                    stalls[k] = (best_true[k] >= 0.0 && rr[k] > 0.25 * best_true[k]) ? stalls[k] + 1 : 0;
+                    if (best_true[k] < 0.0 || rr[k] < best_true[k]) best_true[k] = rr[k];
+                    if (stalls[k] >= kStallConfirms) {
+                        st_p[k] = FFP_ERR_NOT_CONVERGED;
+                        done[k] = 1;
+                    } else {
+                        fresh[k] = 1;
+                    }
                 }
         }
         bool any = false;

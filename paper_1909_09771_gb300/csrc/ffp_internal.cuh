@@ -624,6 +624,11 @@ struct Ws {
     int *flags;    // error flags [16]
 };
 
+// The CG drivers stop with FFP_ERR_NOT_CONVERGED when this many true-residual
+// confirmations in a row fail to halve the best true residual: the tolerance
+// lies below what the FP64 iterate can reach (eps |A||x| / |b|).
+constexpr int kStallConfirms = 3;
+
 constexpr int kRedBlocks = 1216;  // 8 x 152 SMs
 constexpr int kRedSlots = kRedBlocks * 4;
 constexpr int kScal = 64;

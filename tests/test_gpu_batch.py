@@ -210,3 +210,19 @@ def test_full_batched_workload_sampled():
         x, st = P.solve(dev(b), rtol=1e-8, maxit=400)
         assert st["iters"] == stats[p]["iters"]
         assert relerr(host(xs[p]), host(x)) <= 1e-12
+
+
+def test_unreachable_tolerance_pairs_equal_standalone():
+    """The stagnation stop (three confirmations that do not halve the true
+    residual) decides per pair exactly as the single-instance driver does."""
+    inst = instances(3)
+    bat = make_batch(inst, "fp32", "combo")
+    _, stats = bat.solve(rhs_list(inst), rtol=1e-17, maxit=3000, check=False)
+    for i, (w, bs) in enumerate(inst):
+        P = ffp.Preconditioner(w["grid"], dev(w["kappa"]), w["bc"], "fp32", precond="combo")
+        for j, b in enumerate(bs):
+            _, st = P.solve(dev(b), rtol=1e-17, maxit=3000, check=False)
+            s = stats[i * NRHS + j]
+            # tiny grids may meet even 1e-17 exactly; the others must stop on the stall rule
+            assert s["status"] == st["status"] and st["status"] in (0, ffp.FFP_ERR_NOT_CONVERGED), (i, j, s, st)
+            assert s["iters"] == st["iters"] < 600 and s["iters_rec"] == st["iters_rec"], (i, j)

@@ -321,3 +321,17 @@ def test_apply_symmetric_positive_layered128(precision):
     assert abs(a - b) <= tol * (float(torch.norm(Bu)) * float(torch.norm(v)))
     assert float(torch.dot(u, Bu)) > 0
     assert torch.equal(P.apply(u), Bu)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_unreachable_tolerance_stops_early(precision):
+    """rtol below what an FP64 iterate can reach (1e-17 < eps): the recursive
+    residual still meets it, the true residual confirmations stop improving,
+    and the solve ends with FFP_ERR_NOT_CONVERGED long before maxit, with the
+    iterate as accurate as FP64 allows."""
+    w = I.random_small((24, 20, 16), 77, contrast_exp=3)
+    P = ffp.Preconditioner(w["grid"], dev(w["kappa"]), w["bc"], precision, precond="combo")
+    _, st = P.solve(dev(w["b"]), rtol=1e-17, maxit=3000, check=False)
+    assert st["status"] == ffp.FFP_ERR_NOT_CONVERGED
+    assert 0 < st["iters_rec"] < st["iters"] < 600
+    assert st["rel_res_true"] < 1e-12
