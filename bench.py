@@ -283,6 +283,7 @@ def run_ours(args):
             "learned (conv net on log10 kappa, weights " + os.path.basename(args.weights) + ")",
             "rtol": args.rtol,
             "setup_ms": setup_ms,
+            "solve_ms": ms - setup_ms,
             "iters": st["iters"],
             "iters_rec": st["iters_rec"],
             "rel_res_true": st["rel_res_true"],
