@@ -116,67 +116,8 @@ __device__ __forceinline__ void load_line_factor(const LineMap &L, int lane, int
 // from the twist cell outwards.  Each sweep is a first-order affine recurrence
 // along a chain, evaluated as lane-local composition + a 16-lane scan +
 // lane-local substitution.  b/x are per-slot registers; bm/xm the twist cell.
-// x may alias b.
-template <int S, typename R>
-__device__ __forceinline__ void twisted_solve(const LineFactor<S, R> &f, int cnt, int lane,
-                                              const R (&b)[S], R bm, R (&x)[S], R &xm) {
-    const int j = lane & 15;
-    const unsigned FULL = 0xffffffffu;
-    // ---- lower sweep: y[c] = minv (b - ein y[c-1]) = al * y[c-1] + be
-    R al[S];
-    R A = R(1), B = R(0);
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const bool v = s < cnt;
-        const R a_ = v ? -f.minv[s] * f.ein[s] : R(1);
-        const R be = v ? f.minv[s] * b[s] : R(0);
-        al[s] = a_;
-        x[s] = be;
-        B = fma(a_, B, be);
-        A = A * a_;
-    }
-#pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {
-        const R Au = __shfl_up_sync(FULL, A, d, 16);
-        const R Bu = __shfl_up_sync(FULL, B, d, 16);
-        if (j >= d) { B = fma(A, Bu, B); A = A * Au; }
-    }
-    R c = __shfl_up_sync(FULL, B, 1, 16);
-    if (j == 0) c = R(0);
-#pragma unroll
-    for (int s = 0; s < S; ++s) { c = fma(al[s], c, x[s]); x[s] = c; }
-    const R ytop = __shfl_sync(FULL, B, 15);   // y at cell m-1 (0 if the top chain is empty)
-    const R ybot = __shfl_sync(FULL, B, 31);   // y at cell m+1
-    const R ym = f.minv_m * (bm - f.em1 * ytop - f.em * ybot);
-    // ---- upper sweep: x[c] = y[c] - minv eout x[c+1] = y[c] + ga * x[c+1], x[end] = xm
-    R ga[S];
-    R G = R(1);
-    B = R(0);
-#pragma unroll
-    for (int s = S - 1; s >= 0; --s) {
-        const bool v = s < cnt;
-        const R g_ = v ? -f.minv[s] * f.eout[s] : R(1);
-        const R yy = v ? x[s] : R(0);
-        ga[s] = g_;
-        x[s] = yy;
-        B = fma(g_, B, yy);
-        G = G * g_;
-    }
-#pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {
-        const R Gd = __shfl_down_sync(FULL, G, d, 16);
-        const R Bd = __shfl_down_sync(FULL, B, d, 16);
-        if (j + d < 16) { B = fma(G, Bd, B); G = G * Gd; }
-    }
-    const R Gn = __shfl_down_sync(FULL, G, 1, 16);
-    const R Bn = __shfl_down_sync(FULL, B, 1, 16);
-    c = (j == 15) ? ym : fma(Gn, ym, Bn);
-#pragma unroll
-    for (int s = S - 1; s >= 0; --s) { c = fma(ga[s], c, x[s]); x[s] = c; }
-    xm = ym;
-}
-
-// Same solve, re-associated for a short critical path (used by the apply).
+// This is the apply's form, associated for a short critical path; the setup's
+// form (twisted_solve_split, ffp_plane.cuh) splits the slots over two warps.
 // Forward: lane-local prefixes y[s] = pa[s] * c + pb[s] of the affine chain,
 // with c the value entering the lane.  Backward: x[s] = Xb[s] + Xa[s] * c +
 // Gs[s] * cin, where Xb, Xa, Gs are the lane-local suffix compositions of
@@ -310,8 +251,8 @@ __device__ __forceinline__ void twisted_solve_pre(const R (&al)[S], const R (&ga
 // evaluated projectively: M = p/q with (p, q) <- (D p - e^2 q, p), i.e. a
 // product of 2x2 matrices, scanned across the 16 lanes of a chain (scaled by
 // powers of two, which leaves p/q unchanged) and then substituted slot by
-// slot from the lane's incoming (p, q).  FP64.  Returns 1/M per slot and for
-// the twist cell; `bad` is set if a pivot is not positive and finite.
+// slot from the lane's incoming (p, q), in FP64 (the setup's form is
+// twisted_pivots_split in ffp_setup.cuh; the ILU(0) pivots use the same scheme).
 //
 // The scale is 2^-e, e the binary exponent of the largest magnitude.  It is
 // read from the IEEE-754 bit patterns with integer operations, so that only
@@ -357,69 +298,6 @@ __device__ __forceinline__ void scale2(double &a, double &b) {
     a = v[0]; b = v[1];
 }
 
-template <int S>
-__device__ __forceinline__ void twisted_pivots(int cnt, int lane, const double (&D)[S],
-                                               const double (&ein)[S], double Dm, double em1,
-                                               double em, double (&minv)[S], double &minv_m,
-                                               bool &bad) {
-    const int j = lane & 15;
-    const unsigned FULL = 0xffffffffu;
-    // lane-local product P = E_{S-1} ... E_0, E = [[D, -e^2], [1, 0]]
-    double p11 = 1.0, p12 = 0.0, p21 = 0.0, p22 = 1.0;
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        if (s < cnt) {
-            const double e2 = ein[s] * ein[s];
-            const double n11 = D[s] * p11 - e2 * p21;
-            const double n12 = D[s] * p12 - e2 * p22;
-            p21 = p11; p22 = p12; p11 = n11; p12 = n12;
-        }
-    }
-    scale4(p11, p12, p21, p22);
-    // inclusive scan: lane j <- (lane j) x (lane j-d)
-#pragma unroll
-    for (int d = 1; d < 16; d <<= 1) {
-        const double q11 = __shfl_up_sync(FULL, p11, d, 16);
-        const double q12 = __shfl_up_sync(FULL, p12, d, 16);
-        const double q21 = __shfl_up_sync(FULL, p21, d, 16);
-        const double q22 = __shfl_up_sync(FULL, p22, d, 16);
-        if (j >= d) {
-            const double n11 = p11 * q11 + p12 * q21;
-            const double n12 = p11 * q12 + p12 * q22;
-            const double n21 = p21 * q11 + p22 * q21;
-            const double n22 = p21 * q12 + p22 * q22;
-            p11 = n11; p12 = n12; p21 = n21; p22 = n22;
-            scale4(p11, p12, p21, p22);
-        }
-    }
-    // incoming (p, q) = first column of the prefix of lane j-1 ((1, 0) for lane 0)
-    double pp = __shfl_up_sync(FULL, p11, 1, 16);
-    double qq = __shfl_up_sync(FULL, p21, 1, 16);
-    if (j == 0) { pp = 1.0; qq = 0.0; }
-    scale2(pp, qq);
-    bool b_ = false;
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        if (s < cnt) {
-            const double e2 = ein[s] * ein[s];
-            const double np = D[s] * pp - e2 * qq;
-            qq = pp;
-            pp = np;
-            const double mi = qq / pp;
-            minv[s] = mi;
-            b_ |= !(mi > 0.0) || !isfinite(mi);
-        } else {
-            minv[s] = 0.0;
-        }
-    }
-    // chain ends: 1/M_{m-1} = q/p of the top prefix (lane 15), 1/M_{m+1} of lane 31
-    const double t_inv = __shfl_sync(FULL, p21, 15) / __shfl_sync(FULL, p11, 15);
-    const double b_inv = __shfl_sync(FULL, p21, 31) / __shfl_sync(FULL, p11, 31);
-    const double Mm = Dm - em1 * em1 * t_inv - em * em * b_inv;
-    minv_m = 1.0 / Mm;
-    b_ |= !(Mm > 0.0) || !isfinite(Mm);
-    bad = b_;
-}
 
 // ---------------------------------------------------------------- factor line records
 // The apply reads the stored factors line by line in the warp's own order, so

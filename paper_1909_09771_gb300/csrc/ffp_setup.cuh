@@ -12,7 +12,8 @@
 //           half, saved for the twist plane.
 //   phase 1 (1 CTA): P_mz = Dhat_mz - (term from mz-1) - (term from mz+1), then
 //     its level-2 factorization.
-// Level 2 (lines of P_i), twisted at my = floor((ny-1)/2), warps 0 and 1:
+// Level 2 (lines of P_i), twisted at my = floor((ny-1)/2), two warps per half
+// that split every line's slots (warps 0/2 and 1/3, see SlotSplit):
 //   T_0 = Dbar_0 / T_{ny-1} = Dbar_{ny-1}; T_k = Dbar_k - p X p with
 //   X = 2 beta - beta T_prev beta, beta = (T_prev^{-1} w) ./ w, w = p .* t_k,
 //   p = y-band of P_i between the two lines; the twist line takes both terms.
@@ -44,70 +45,157 @@ struct SetupPol {
     __device__ __forceinline__ void put_out(int k, int a, double u) const { V[(long)k * nx + a] = u; }
 };
 
-// State of the previous line T_prev as seen by this lane.
+// State of the previous line T_prev as seen by this lane (this part's slots).
 template <int S>
 struct LineState {
     LineFactor<S, double> f;
     double Td[S], To[S], Tdm, Tom;
 };
 
+// twisted_pivots (level 1) with the slots split over the two parts of sp:
+// each part multiplies its own slots' 2x2 matrices, the lane's product is
+// formed from both, both parts scan it, and part 1 enters its slots with part
+// 0's product applied.  minv is valid on this part's slots.
+template <int S>
+__device__ __forceinline__ void twisted_pivots_split(int cnt, int lane, const double (&D)[S],
+                                                     const double (&ein)[S], double Dm, double em1,
+                                                     double em, double (&minv)[S], double &minv_m,
+                                                     bool &bad, SlotSplit &sp) {
+    const int j = lane & 15;
+    const unsigned FULL = 0xffffffffu;
+    // this part's product E_{s1-1} ... E_{s0}, E = [[D, -e^2], [1, 0]] (pads are identity)
+    double p11 = 1.0, p12 = 0.0, p21 = 0.0, p22 = 1.0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (sp.mine(s) && s < cnt) {
+            const double e2 = ein[s] * ein[s];
+            const double n11 = D[s] * p11 - e2 * p21;
+            const double n12 = D[s] * p12 - e2 * p22;
+            p21 = p11; p22 = p12; p11 = n11; p12 = n12;
+        }
+    }
+    // P0 = part 0's product, P1 = part 1's; the lane's product is P1 P0
+    double a11, a12, a21, a22, f11, f12, f21, f22;
+    {
+        const double mv[4] = {p11, p12, p21, p22};
+        double o[4];
+        sp.swap<4>(mv, o, lane);
+        const double b11 = sp.part ? p11 : o[0], b12 = sp.part ? p12 : o[1];
+        const double b21 = sp.part ? p21 : o[2], b22 = sp.part ? p22 : o[3];
+        a11 = sp.part ? o[0] : p11; a12 = sp.part ? o[1] : p12;
+        a21 = sp.part ? o[2] : p21; a22 = sp.part ? o[3] : p22;
+        f11 = b11 * a11 + b12 * a21;
+        f12 = b11 * a12 + b12 * a22;
+        f21 = b21 * a11 + b22 * a21;
+        f22 = b21 * a12 + b22 * a22;
+    }
+    scale4(f11, f12, f21, f22);
+    // inclusive scan: lane j <- (lane j) x (lane j-d)
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const double q11 = __shfl_up_sync(FULL, f11, d, 16);
+        const double q12 = __shfl_up_sync(FULL, f12, d, 16);
+        const double q21 = __shfl_up_sync(FULL, f21, d, 16);
+        const double q22 = __shfl_up_sync(FULL, f22, d, 16);
+        if (j >= d) {
+            const double n11 = f11 * q11 + f12 * q21;
+            const double n12 = f11 * q12 + f12 * q22;
+            const double n21 = f21 * q11 + f22 * q21;
+            const double n22 = f21 * q12 + f22 * q22;
+            f11 = n11; f12 = n12; f21 = n21; f22 = n22;
+            scale4(f11, f12, f21, f22);
+        }
+    }
+    // incoming (p, q) = first column of the prefix of lane j-1 ((1, 0) for lane 0);
+    // part 1 enters its first slot after part 0's slots
+    double pp = __shfl_up_sync(FULL, f11, 1, 16);
+    double qq = __shfl_up_sync(FULL, f21, 1, 16);
+    if (j == 0) { pp = 1.0; qq = 0.0; }
+    scale2(pp, qq);
+    if (sp.part) {
+        const double np = a11 * pp + a12 * qq, nq = a21 * pp + a22 * qq;
+        pp = np;
+        qq = nq;
+        scale2(pp, qq);
+    }
+    bool b_ = false;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (!sp.mine(s)) continue;
+        if (s < cnt) {
+            const double e2 = ein[s] * ein[s];
+            const double np = D[s] * pp - e2 * qq;
+            qq = pp;
+            pp = np;
+            const double mi = qq / pp;
+            minv[s] = mi;
+            b_ |= !(mi > 0.0) || !isfinite(mi);
+        } else {
+            minv[s] = 0.0;
+        }
+    }
+    // chain ends: 1/M_{m-1} = q/p of the top prefix (lane 15), 1/M_{m+1} of lane 31
+    const double t_inv = __shfl_sync(FULL, f21, 15) / __shfl_sync(FULL, f11, 15);
+    const double b_inv = __shfl_sync(FULL, f21, 31) / __shfl_sync(FULL, f11, 31);
+    const double Mm = Dm - em1 * em1 * t_inv - em * em * b_inv;
+    minv_m = 1.0 / Mm;
+    b_ |= !(Mm > 0.0) || !isfinite(Mm);
+    bad = b_;
+}
+
 // beta of the level-2 Schur term from T_prev onto the line with coupling p
 // (global, this line's cells) and filter tl (or NULL): returns the terms
-// cd = p X p (diagonal) and co = p X p (x-band) per slot and for the twist cell.
+// cd = p X p (diagonal) and co = p X p (x-band) per slot of this part and for
+// the twist cell.
 template <int S>
 __device__ __forceinline__ void line_schur(const LineMap &L, int nx, int lane, int cnt,
                                            const LineState<S> &st, const double *p,
                                            const double *tl, double *SB, double *SP,
                                            double (&cd)[S], double (&co)[S], double &cdm,
-                                           double &com) {
+                                           double &com, SlotSplit &sp) {
     double w[S], wm, pa[S], pm;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        if (s < cnt) {
+        pa[s] = 0.0; w[s] = 0.0;
+        if (sp.mine(s) && s < cnt) {
             const int a = slot_cell<S>(L, lane, s);
             pa[s] = p[a];
             w[s] = pa[s] * (tl ? tl[a] : 1.0);
-        } else {
-            pa[s] = 0.0; w[s] = 0.0;
         }
     }
     pm = p[L.m];
     wm = pm * (tl ? tl[L.m] : 1.0);
     double v[S], vm;
-    twisted_solve<S, double>(st.f, cnt, lane, w, wm, v, vm);  // v = T_prev^{-1} w
+    twisted_solve_split<S, double>(st.f, cnt, lane, w, wm, v, vm, sp);  // v = T_prev^{-1} w
     double be[S], bem;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        if (s < cnt) {
-            const bool z = fabs(w[s]) < 1e-300;   // one divide either way
+        be[s] = 0.0;
+        if (sp.mine(s) && s < cnt) {
+            const bool z = fabs(w[s]) < 1e-300;  // one divide either way
             be[s] = (z ? 1.0 : v[s]) / (z ? st.Td[s] : w[s]);
             const int a = slot_cell<S>(L, lane, s);
             SB[a] = be[s];
             SP[a] = pa[s];
-        } else {
-            be[s] = 0.0;
         }
     }
     {
         const bool z = fabs(wm) < 1e-300;
         bem = (z ? 1.0 : vm) / (z ? st.Tdm : wm);
     }
-    if (lane == 0) { SB[L.m] = bem; SP[L.m] = pm; }
-    __syncwarp();
+    if (lane == 0 && sp.part == 0) { SB[L.m] = bem; SP[L.m] = pm; }
+    sp.sync();
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        if (s < cnt) {
+        cd[s] = 0.0; co[s] = 0.0;
+        if (sp.mine(s) && s < cnt) {
             const int a = slot_cell<S>(L, lane, s);
             const double xd = 2.0 * be[s] - be[s] * st.Td[s] * be[s];
             cd[s] = pa[s] * xd * pa[s];
             if (a + 1 < nx) {
                 const double xo = -be[s] * st.To[s] * SB[a + 1];
                 co[s] = pa[s] * xo * SP[a + 1];
-            } else {
-                co[s] = 0.0;
             }
-        } else {
-            cd[s] = 0.0; co[s] = 0.0;
         }
     }
     {
@@ -120,32 +208,31 @@ __device__ __forceinline__ void line_schur(const LineMap &L, int nx, int lane, i
             com = 0.0;
         }
     }
-    __syncwarp();
+    sp.sync();
 }
 
-// Twisted pivots of T = tridiag(To, Td, To) of one line -> line state.
+// Twisted pivots of T = tridiag(To, Td, To) of one line -> line state (this part's slots).
 template <int S>
 __device__ __forceinline__ void factor_line(const LineMap &L, int lane, int cnt,
                                             const double (&Td)[S], const double (&To)[S],
                                             double Tdm, double Tom, double *SO,
-                                            LineState<S> &st, int *flags) {
+                                            LineState<S> &st, int *flags, SlotSplit &sp) {
 #pragma unroll
     for (int s = 0; s < S; ++s)
-        if (s < cnt) SO[slot_cell<S>(L, lane, s)] = To[s];
-    if (lane == 0) SO[L.m] = Tom;
-    __syncwarp();
+        if (sp.mine(s) && s < cnt) SO[slot_cell<S>(L, lane, s)] = To[s];
+    if (lane == 0 && sp.part == 0) SO[L.m] = Tom;
+    sp.sync();
     double ein[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        if (s < cnt) {
+        st.f.ein[s] = 0.0; st.f.eout[s] = 0.0; ein[s] = 0.0;
+        if (sp.mine(s) && s < cnt) {
             const int a = slot_cell<S>(L, lane, s);
             const double e_lo = (a > 0) ? SO[a - 1] : 0.0;
             const double e_hi = To[s];
             if (lane < 16) { st.f.ein[s] = e_lo; st.f.eout[s] = e_hi; }
             else { st.f.ein[s] = e_hi; st.f.eout[s] = e_lo; }
             ein[s] = st.f.ein[s];
-        } else {
-            st.f.ein[s] = 0.0; st.f.eout[s] = 0.0; ein[s] = 0.0;
         }
         st.Td[s] = Td[s];
         st.To[s] = To[s];
@@ -155,23 +242,26 @@ __device__ __forceinline__ void factor_line(const LineMap &L, int lane, int cnt,
     st.Tdm = Tdm;
     st.Tom = Tom;
     bool bad = false;
-    twisted_pivots<S>(cnt, lane, Td, ein, Tdm, st.f.em1, st.f.em, st.f.minv, st.f.minv_m, bad);
+    twisted_pivots_split<S>(cnt, lane, Td, ein, Tdm, st.f.em1, st.f.em, st.f.minv, st.f.minv_m, bad, sp);
     if (bad) atomicOr(flags + FL_BREAKDOWN, 1);
-    __syncwarp();
+    sp.sync();
 }
 
-// Store line k of the plane: FP64 natural-order copies for the setup's own
-// plane solves (l1d, mid), the natural-order l1 (for export) and the line
-// record line0 + k: the line solve's multipliers -1/M * coupling (forward and
-// backward), 1/M and the twist cell.
+// Store line k of the plane (this part's slots; the twist cell by part 0):
+// FP64 natural-order copies for the setup's own plane solves (l1d, mid), the
+// natural-order l1 (for export) and the line record line0 + k: the line
+// solve's multipliers -1/M * coupling (forward and backward), 1/M and the
+// twist cell.
 template <int S>
 __device__ __forceinline__ void store_line(const LineMap &L, int lane, int cnt, int nx, int k,
                                            const LineState<S> &st, double *l1d, double *mid,
-                                           void *rec, void *l1n, long line0, int prec) {
+                                           void *rec, void *l1n, long line0, int prec,
+                                           const SlotSplit &sp) {
     const long o = (long)k * nx;
     const long rb = (line0 + k) * rec_len(S);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
+        if (!sp.mine(s)) continue;
         const bool v = s < cnt;
         if (v) {
             const int a = slot_cell<S>(L, lane, s);
@@ -183,7 +273,7 @@ __device__ __forceinline__ void store_line(const LineMap &L, int lane, int cnt, 
         put_factor(rec, rb + rec_slot(S, REC_GAMMA, lane, s), v ? -st.f.minv[s] * st.f.eout[s] : 1.0, prec);
         put_factor(rec, rb + rec_slot(S, REC_MINV, lane, s), v ? st.f.minv[s] : 0.0, prec);
     }
-    if (lane == 0) {
+    if (lane == 0 && sp.part == 0) {
         l1d[o + L.m] = st.Tom;
         mid[o + L.m] = st.f.minv_m;
         put_factor(l1n, (line0 + k) * nx + L.m, st.Tom, prec);
@@ -194,15 +284,16 @@ __device__ __forceinline__ void store_line(const LineMap &L, int lane, int cnt, 
     }
 }
 
-// Level-2 factorization of one plane (warps 0 and 1).  Pd/Px/Py: bands of P
-// (plane slice, FP64); tp: filter on the plane or NULL; outputs the FP64 line
-// factors (l1d, mid) used by the nested plane solve and the stored factors.
+// Level-2 factorization of one plane (warps 0-3: half wid = warp & 1 on two
+// warps that split the slots).  Pd/Px/Py: bands of P (plane slice, FP64); tp:
+// filter on the plane or NULL; outputs the FP64 line factors (l1d, mid) used
+// by the nested plane solve and the stored factors.
 template <int S>
 __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
                              const double *Px, const double *Py, const double *tp, double *l1d,
                              double *mid, void *rec, void *l1n, long line0, int prec,
                              double *lbuf, double *meet, int wid, int lane, int cnt,
-                             int *flags) {
+                             int *flags, SlotSplit &sp) {
     const int my = (ny - 1) / 2;
     const int nl = (wid == 0) ? my : ny - 1 - my;
     double *SB = lbuf + wid * 3 * nx, *SP = SB + nx, *SO = SP + nx;
@@ -213,12 +304,11 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
         const long o = (long)k * nx;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            if (s < cnt) {
+            Td[s] = 1.0; To[s] = 0.0;
+            if (sp.mine(s) && s < cnt) {
                 const int a = slot_cell<S>(L, lane, s);
                 Td[s] = Pd[o + a];
                 To[s] = Px[o + a];
-            } else {
-                Td[s] = 1.0; To[s] = 0.0;
             }
         }
         Tdm = Pd[o + L.m];
@@ -226,14 +316,15 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
         if (t > 0) {
             const int kc = (wid == 0) ? k - 1 : k;
             line_schur<S>(L, nx, lane, cnt, st, Py + (long)kc * nx, tp ? tp + o : nullptr, SB, SP,
-                          cd, co, cdm, com);
+                          cd, co, cdm, com, sp);
 #pragma unroll
-            for (int s = 0; s < S; ++s) { Td[s] -= cd[s]; To[s] -= co[s]; }
+            for (int s = 0; s < S; ++s)
+                if (sp.mine(s)) { Td[s] -= cd[s]; To[s] -= co[s]; }
             Tdm -= cdm;
             Tom -= com;
         }
-        factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags);
-        store_line<S>(L, lane, cnt, nx, k, st, l1d, mid, rec, l1n, line0, prec);
+        factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags, sp);
+        store_line<S>(L, lane, cnt, nx, k, st, l1d, mid, rec, l1n, line0, prec, sp);
     }
     // twist line: Schur terms from both halves
     {
@@ -241,7 +332,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
         const int kc = (wid == 0) ? my - 1 : my;
         if (nl > 0) {
             line_schur<S>(L, nx, lane, cnt, st, Py + (long)kc * nx, tp ? tp + o : nullptr, SB, SP,
-                          cd, co, cdm, com);
+                          cd, co, cdm, com, sp);
         } else {
 #pragma unroll
             for (int s = 0; s < S; ++s) { cd[s] = 0.0; co[s] = 0.0; }
@@ -250,27 +341,26 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
         double *MD = meet + wid * 2 * nx, *MO = MD + nx;
 #pragma unroll
         for (int s = 0; s < S; ++s)
-            if (s < cnt) {
+            if (sp.mine(s) && s < cnt) {
                 const int a = slot_cell<S>(L, lane, s);
                 MD[a] = cd[s];
                 MO[a] = co[s];
             }
-        if (lane == 0) { MD[L.m] = cdm; MO[L.m] = com; }
-        named_barrier(2, 64);
+        if (lane == 0 && sp.part == 0) { MD[L.m] = cdm; MO[L.m] = com; }
+        named_barrier(2, 128);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            if (s < cnt) {
+            Td[s] = 1.0; To[s] = 0.0;
+            if (sp.mine(s) && s < cnt) {
                 const int a = slot_cell<S>(L, lane, s);
                 Td[s] = Pd[o + a] - meet[a] - meet[2 * nx + a];
                 To[s] = Px[o + a] - meet[nx + a] - meet[3 * nx + a];
-            } else {
-                Td[s] = 1.0; To[s] = 0.0;
             }
         }
         Tdm = Pd[o + L.m] - meet[L.m] - meet[2 * nx + L.m];
         Tom = Px[o + L.m] - meet[nx + L.m] - meet[3 * nx + L.m];
-        factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags);
-        if (wid == 0) store_line<S>(L, lane, cnt, nx, my, st, l1d, mid, rec, l1n, line0, prec);
+        factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags, sp);
+        if (wid == 0) store_line<S>(L, lane, cnt, nx, my, st, l1d, mid, rec, l1n, line0, prec, sp);
     }
 }
 
@@ -281,8 +371,13 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
     const long nxy = (long)nx * ny;
     double *gbuf = sm;                 // plane solve exchange [2][2][nx]
     double *lbuf = sm + 4 * nx;        // level-2 line buffers [2 warps][3][nx]
-    double *meet = sm + 10 * nx;       // level-2 twist exchange [2 warps][2][nx]
+    double *meet = sm + 10 * nx;       // level-2 twist exchange [2 halves][2][nx]
+    double *ex = sm + 14 * nx;         // slot-split exchange [2 halves][512]
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // warps 0-3 run the level-2 work: half wid & 1, slot part wid >> 1, so the four
+    // warps sit on the four scheduler partitions (pair barriers 3 and 4)
+    const int half = wid & 1;
+    SlotSplit sp = make_split<S>(wid >> 1, ex + half * 512, 3 + half);
     const LineMap L(nx);
     const int cnt = lane_count<S>(L, lane);
     const int mz = (nz - 1) / 2;
@@ -304,20 +399,20 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
                 put_factor(A.rec, ((long)i * ny + e / nx) * rec_len(S) +
                                       rec_cell(nx, S, REC_L2, MID_L2, (int)(e % nx)),
                            Py[e], A.prec);
-            if (wid < 2)
+            if (wid < 4)
                 level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + i * nxy : nullptr, l1d, mid,
-                                A.rec, A.l1n, (long)i * ny, A.prec, lbuf, meet, wid, lane, cnt,
-                                flags);
+                                A.rec, A.l1n, (long)i * ny, A.prec, lbuf, meet, half, lane, cnt,
+                                flags, sp);
             const int dst = (t == nl3 - 1) ? mz : ((h == 0) ? i + 1 : i - 1);
             const int ic = (i < dst) ? i : dst;
             const double *C = A.cz + ic * nxy;
             for (long e = tid; e < nxy; e += blockDim.x)
                 W[e] = C[e] * (A.t ? A.t[dst * nxy + e] : 1.0);
             __syncthreads();
-            if (wid < 2) {
+            if (wid < 4) {
                 SetupPol pol{W, V, nx};
-                plane_solve<S, false, double, double>(L, nx, ny, l1d, mid, Py, pol, gbuf, wid, lane,
-                                                      cnt);
+                plane_solve<S, false, double, double>(L, nx, ny, l1d, mid, Py, pol, gbuf, half, lane,
+                                                      cnt, sp);
             }
             __syncthreads();
             for (long e = tid; e < nxy; e += blockDim.x) {
@@ -367,10 +462,10 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
                        vy, A.prec);
         }
         __syncthreads();
-        if (wid < 2)
+        if (wid < 4)
             level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + g0 : nullptr, A.ws.sF[0][0],
-                            A.ws.sF[0][1], A.rec, A.l1n, (long)mz * ny, A.prec, lbuf, meet, wid,
-                            lane, cnt, flags);
+                            A.ws.sF[0][1], A.rec, A.l1n, (long)mz * ny, A.prec, lbuf, meet, half,
+                            lane, cnt, flags, sp);
     }
 }
 
@@ -386,7 +481,7 @@ __global__ void __launch_bounds__(256) setup_kernel(const __grid_constant__ Setu
 
 template <int S>
 cudaError_t setup_table_for_slots(const SetupArgs *table, int count, int nx_max, cudaStream_t st) {
-    const size_t smem = sizeof(double) * 14 * (size_t)nx_max;
+    const size_t smem = sizeof(double) * (14 * (size_t)nx_max + 1024);
     cudaError_t e = cudaFuncSetAttribute(setup_kernel<S>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -401,7 +496,7 @@ template <int S>
 cudaError_t setup_for_slots(const KernelCtx &c, const double *t, cudaStream_t st) {
     SetupArgs a;
     fill_setup_args(c, t, &a);
-    const size_t smem = sizeof(double) * 14 * (size_t)a.nx;
+    const size_t smem = sizeof(double) * (14 * (size_t)a.nx + 1024);
     cudaError_t e = cudaFuncSetAttribute(setup_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
