@@ -249,7 +249,12 @@ class Preconditioner:
 
     def solve(self, b, x=None, rtol=1e-8, maxit=200, stream=None, check=True):
         """PCG / flexible CG; returns (x, stats dict).  x (if given) is x0 and is
-        overwritten with the solution."""
+        overwritten with the solution.  The stats are those of ffp_stats: iters,
+        iters_rec (first iteration at which the recursive residual met rtol),
+        status, rel_res, rel_res_true, solve_s, precond_ms, ntd_ms, napply,
+        launches.  A status of FFP_ERR_NOT_CONVERGED means maxit was reached or
+        the true residual stopped falling (rtol below the FP64 floor); with
+        check=True any status but FFP_OK raises FFPError."""
         b = _dev_vec(b, self.n, "b")
         x = torch.zeros_like(b) if x is None else _dev_vec(x, self.n, "x")
         s = Stats()
