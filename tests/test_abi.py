@@ -56,3 +56,33 @@ def test_strerror_and_null_args(lib):
     g = ffp.Grid(4, 4, 4, 1, 1, 1)
     assert lib.ffp_setup(ctypes.byref(g), None, None, 0, None, 0, 0, None, 0, None,
                          ctypes.byref(h)) == ffp.FFP_ERR_ARG
+
+
+def test_struct_layouts_match_binding(tmp_path):
+    """The ctypes mirrors of ffp_grid, ffp_bc, ffp_stats and ffp_batch_config
+    have the size and field offsets a C compiler gives the structs of
+    include/ffp.h (a mismatch would corrupt every call that passes them)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    mirrors = {"ffp_grid": ffp.Grid, "ffp_bc": ffp.BC, "ffp_stats": ffp.Stats,
+               "ffp_batch_config": ffp.BatchConfig}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HDR}"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
