@@ -187,17 +187,22 @@ int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, dou
  *   r, z    device FP64 [N], distinct (as for ffp_apply)
  * Returns FFP_ERR_ARG if the grid's planes do not fit the fixed scratch -- if
  * nx * ny > FFP_NOALLOC_MAX_PLANE, or if one plane in the apply's line-block
- * layout (ny * 32 * (S + 1) values of its arithmetic type, FP64 for FP64
- * factors, FP32 otherwise; S = the smallest of 1, 2, 3, 4, 6, 8, 11, 16, 22,
- * 32 with 16 S >= nx - 1 - floor((nx - 1) / 2)) takes more than
- * FFP_NOALLOC_MAX_PLANE * 8 bytes -- or if the current device is not the
- * handle's.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture on that device.  All calls share the
- * one array: calls whose kernels overlap on the GPU (on different streams, or
- * from several host threads) race on it and must be serialised by the caller.
- * Nothing in the array needs clearing: each call writes every scratch entry
- * before reading it. */
+ * layout takes more than FFP_NOALLOC_MAX_PLANE * 8 bytes.  That plane holds
+ * ny * (32 * SP + 32) values of the apply's arithmetic type (FP64 for FP64
+ * factors, FP32 otherwise), where S is the smallest of 1, 2, 3, 4, 6, 8, 11,
+ * 16, 22, 32 with 16 S >= nx - 1 - floor((nx - 1) / 2) and SP is S rounded up
+ * to a multiple of 4 (for example nx = 3, ny = 1000 with FP64 factors needs
+ * 1000 * 160 * 8 bytes and is rejected).  It also returns FFP_ERR_ARG if the
+ * current device is not the handle's.
+ * The first call on a device looks up the array's device address in the
+ * device's primary context (the one the CUDA runtime uses) and caches it for
+ * the life of the process; make that first call before any stream capture on
+ * that device.  cudaDeviceReset destroys that context, and the cached address
+ * with it: do not call this entry point again after a reset of its device.
+ * All calls share the one array: calls whose kernels overlap on the GPU (on
+ * different streams, or from several host threads) race on it and must be
+ * serialised by the caller.  Nothing in the array needs clearing: each call
+ * writes every scratch entry before reading it. */
 #define FFP_NOALLOC_MAX_PLANE 131072
 int ffp_apply_noalloc(ffp_handle *h, const double *r, double *z, void *stream);
 

@@ -409,22 +409,6 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
 __device__ __forceinline__ void mbar_arrive_cpasync(unsigned long long *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// arrive and add `bytes` to the transaction count of the current phase
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
-                 ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
-// completion reported to the mbarrier as transaction bytes
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
-                                         unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
 // One bounded try of the phase with the given parity (acquire at CTA scope).
 __device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parity) {
     unsigned ok;

@@ -142,3 +142,24 @@ def test_filter_target_is_positive_floored_and_mean_free():
     assert np.all(t >= 0.05) and t.max() == 1.0
     assert abs(s.mean()) <= 1e-14
     assert np.allclose(np.exp(s) / np.exp(s).max(), t)
+
+
+def test_filter_target_golden_two_ritz_pairs():
+    """The target against a hand-derived fixture (tests/golden/filter_target_two_ritz.txt):
+    two Ritz pairs, per-vector max-normalisation, weights theta_0 / theta_k,
+    the square root of the weighted sum, scaling to max 1, the floor and the
+    mean-free log.  Inverting the weights, dropping the normalisation or the
+    square root, or flooring before scaling each changes the values."""
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "filter_target_two_ritz.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    theta = np.array(rows[0])
+    Y = np.array(rows[1:4])
+    for floor, (t_exp, s_exp) in ((0.1, rows[4:6]), (0.6, rows[6:8])):
+        t, s = C.filter_target(theta, Y, nvec=2, floor=floor)
+        np.testing.assert_allclose(t, t_exp, rtol=1e-15)
+        np.testing.assert_allclose(s, s_exp, rtol=1e-14)

@@ -65,3 +65,33 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                         "-p", "no:cacheprovider"], cwd=work, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+# Mistakes planted in the learned-filter oracle (oracle/convnet.py), caught by
+# tests/test_oracle_convnet.py.
+CONVNET_MUTATIONS = {
+    # target weights theta_0 / theta_k, inverted
+    "target_weights_inverted": ("acc += (theta[0] / theta[k]) * y * y",
+                                "acc += (theta[k] / theta[0]) * y * y"),
+    # each Ritz vector scaled to max |y| = 1 before it is weighted
+    "target_no_normalisation": ("y = Y[:, k] / np.max(np.abs(Y[:, k]))", "y = Y[:, k]"),
+    # the floor applies after scaling to max 1
+    "target_floor_before_scaling": ("t = np.maximum(t / t.max(), floor)",
+                                    "t = np.maximum(t, floor) / np.maximum(t, floor).max()"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CONVNET_MUTATIONS))
+def test_convnet_pins_catch_planted_mistake(name, tmp_path):
+    old, new = CONVNET_MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "convnet.py")).read()
+    assert old in src, f"mutation anchor for {name} not found in the convnet oracle"
+    work = tmp_path / "repo"
+    for sub in ("oracle", "tests", "paper_1909_09771_gb300"):
+        shutil.copytree(os.path.join(ROOT, sub), work / sub,
+                        ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*"))
+    (work / "oracle" / "convnet.py").write_text(src.replace(old, new))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_convnet.py", "-q", "-x",
+                        "-p", "no:cacheprovider"], cwd=work, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"

@@ -66,3 +66,26 @@ def test_noalloc_rejects_planes_beyond_the_fixed_scratch(lib):
     st, _ = _noalloc(lib, P, r)
     assert st == ffp.FFP_ERR_ARG
     P.close()
+
+
+@pytest.mark.parametrize("ny, ok", [(800, True), (1000, False)])
+def test_noalloc_line_block_size_rule(lib, ny, ok):
+    """nx = 3 with FP64 factors: S = 1 slot per lane, padded to SP = 4, so one
+    scratch plane in the line-block layout holds ny * (32 * 4 + 32) = 160 ny
+    FP64 values.  The plane has only 3 ny cells (far below the cell limit), so
+    ny = 1000 (1.28 MB > 1 MiB) is rejected by the line-block rule alone, while
+    ny = 800 (1.024 MB) fits and gives ffp_apply's result."""
+    grid = (3, ny, 2)
+    assert grid[0] * grid[1] <= 131072
+    assert (ny * 160 * 8 <= 8 * 131072) == ok
+    w = I.random_small(grid, 43, contrast_exp=3)
+    P = ffp.Preconditioner(grid, torch.as_tensor(w["kappa"], device="cuda"), w["bc"], "fp64")
+    r = torch.as_tensor(np.random.default_rng(3).standard_normal(int(np.prod(grid))), device="cuda")
+    st, z = _noalloc(lib, P, r)
+    if ok:
+        assert st == ffp.FFP_OK
+        z_ref = P.apply(r)
+        assert float(torch.linalg.norm(z - z_ref) / torch.linalg.norm(z_ref)) <= 1e-12
+    else:
+        assert st == ffp.FFP_ERR_ARG
+    P.close()
