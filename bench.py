@@ -2,14 +2,19 @@
 diffusion problem with the nested twisted filtering preconditioner
 (arXiv 1909.09771) on one GB300, setup included.
 
-A step = one full pass of the hot path over one input: operator assembly,
-preconditioner setup, and the (flexible) CG solve to rtol, inputs resident in
-HBM.  `e2e` repeats the step through the public API from pinned host buffers
-(kappa and b copied in, x copied out inside the timed region).
+A step = one full pass of the hot path over one input: the learned filter's
+inference on kappa, operator assembly, preconditioner setup (FP32 factors),
+and the flexible-CG solve to rtol, inputs resident in HBM.  The metric
+compares that form with the plain FP64 one (FP64 factors, rowsum filter, same
+preconditioner and tolerance), which the same run times once on the same GPU
+and reports as config.fp64_rowsum.  `e2e` repeats the step through the public
+API from pinned host buffers (kappa and b copied in, x copied out inside the
+timed region).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload grf350|layered128|blocks32|batched|paper<T>_<n>]
                   [--precision fp32|fp64|bf16] [--precond combo|ntd] [--rtol R]
+                  [--filter learned|rowsum] [--fp64-steps F]
 
 paper<T>_<n> (T = 1, 2, 3; e.g. paper1_350) is the paper's own test matrix of
 type T on n^3 (Sec. IV, Table I); compare with --rtol 1e-7 or 1e-10.
@@ -17,7 +22,7 @@ type T on n^3 (Sec. IV, Table I); compare with --rtol 1e-7 or 1e-10.
 --impl reference times the CPU oracle (plain C, FP64, one core) on a bounded
 sample of the same workload.  Under torchrun (N > 1) the ranks solve
 independent replicas (the single-instance solve does not shard) and rank 0
-prints the aggregate.
+prints the aggregate; the batched workload shards its instance list.
 """
 from __future__ import annotations
 
@@ -41,11 +46,12 @@ RTOL = 1e-8
 L2_BYTES = 129e6
 MAXIT = 1000
 
-# algorithmic bytes per unknown of one B_NTD apply (the three sweep launches):
-# 2 sweeps x 4 factor arrays (l1, 1/M, l2, l3) in the storage precision + 4
-# vector passes (read r, write y, read y, write z) in the apply's arithmetic
-# type (FP64 for FP64 factors, FP32 otherwise)
-NTD_BYTES = {"fp64": 2 * 4 * 8 + 4 * 8, "fp32": 2 * 4 * 4 + 4 * 4, "bf16": 2 * 4 * 2 + 4 * 4}
+# Algorithmic bytes per unknown of one B_NTD apply: 2 sweeps x 4 factor arrays
+# (l1, 1/M, l2, l3) in the storage precision + 4 FP64 vector passes (read r,
+# write y, read y, write z): 96 / 64 / 48 bytes for FP64 / FP32 / BF16 factors.
+NTD_BYTES = {"fp64": 2 * 4 * 8 + 4 * 8, "fp32": 2 * 4 * 4 + 4 * 8, "bf16": 2 * 4 * 2 + 4 * 8}
+# SpMV fused with (p, q): p 8 + q 8 + 4 FP64 bands 32 bytes per unknown.
+SPMV_BYTES = 48
 
 
 def make_workload(name, seed=0):
@@ -150,11 +156,47 @@ def dist_env():
 
 
 def replica_seed(workload, seed, rank):
-    """Seed of rank `rank`'s replica: every rank solves its own independent
-    problem (the solve does not shard), so the ranks' inputs must differ.  A
-    batched replica spans seeds seed' .. seed' + 63 (one per instance), hence
-    the stride of 1000."""
-    return seed + (1000 * rank if workload == "batched" else rank)
+    """Seed of rank `rank`'s replica of a single-instance workload: every rank
+    solves its own independent problem (the solve does not shard), so the
+    ranks' inputs must differ.  (The batched workload is not replicated: its
+    one instance list is partitioned, see lpt_partition.)"""
+    return seed + rank
+
+
+def lpt_partition(sizes, nranks):
+    """Partition instances over ranks by longest-processing-time-first on
+    their size (n = nx ny nz, which sets an instance's setup work and its
+    per-iteration sweep and vector work): instances in decreasing size, each
+    to the rank with the smallest load so far (the lowest rank on ties).
+    Deterministic; returns every rank's instance indices in increasing order.
+    Its load is within one instance of the best balance (Graham's bound:
+    max load <= mean load + largest instance)."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    load = [0] * nranks
+    parts = [[] for _ in range(nranks)]
+    for i in order:
+        r = min(range(nranks), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
+def merge_pair_stats(local_stats, local_instances, nrhs, count, world_size):
+    """Every rank's per-pair statistics in global pair order (instance i,
+    right-hand side j -> i * nrhs + j), gathered to all ranks.  Only these
+    small host records are exchanged; no solver data crosses ranks."""
+    if world_size <= 1:
+        return list(local_stats)
+    import torch.distributed as dist
+    objs = [None] * world_size
+    dist.all_gather_object(objs, (list(local_instances), list(local_stats)))
+    out = [None] * (count * nrhs)
+    for insts, stats in objs:
+        for j, i in enumerate(insts):
+            for r in range(nrhs):
+                out[i * nrhs + r] = stats[j * nrhs + r]
+    assert all(v is not None for v in out)
+    return out
 
 
 def max_over_ranks(values, device, world_size):
@@ -167,6 +209,47 @@ def max_over_ranks(values, device, world_size):
     t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return [float(v) for v in t.tolist()]
+
+
+def solve_step(ffp, grid, bc, precision, precond, work, net, t_buf, rtol, stream):
+    """One pass of the hot path on resident inputs: the learned filter's
+    inference (if any), assembly + setup, and the flexible-CG solve to rtol.
+    Returns a function step(kappa, b, x, marks) -> stats."""
+    import torch
+
+    def step(kap, rhs, xout, marks=None):
+        if marks is not None:
+            marks.append([torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)])
+            marks[-1][0].record(stream)
+        t = net.forward(grid, kap, batch=1, t=t_buf) if net is not None else None
+        P = ffp.Preconditioner(grid, kap, bc, precision, precond=precond, workspace=work, t=t)
+        if marks is not None:
+            marks[-1][1].record(stream)
+        xout.zero_()
+        _, st = P.solve(rhs, x=xout, rtol=rtol, maxit=MAXIT, check=False)
+        P.close()
+        return st
+    return step
+
+
+def timed_steps(step, kappa, b, x, steps, local):
+    """`steps` device-timed steps (CUDA events on the launching stream, a
+    synchronise on both sides); returns (ms per step, setup ms per step, stats,
+    clock summary)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats, marks = [], []
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            stats.append(step(kappa, b, x, marks))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    setup_ms = sum(m0.elapsed_time(m1) for m0, m1 in marks) / len(marks)
+    return ms, setup_ms, stats, clk.summary()
 
 
 def run_ours(args):
@@ -193,54 +276,30 @@ def run_ours(args):
     wsb = ffp.workspace_bytes(grid, args.precision)
     work = torch.empty(wsb, dtype=torch.uint8, device=dev)
 
-    net = None
+    net, t_buf = None, None
     if args.filter == "learned":
         from paper_1909_09771_gb300 import learned as LF
         net = LF.load_weights(args.weights, device=dev)
         t_buf = torch.empty(n, dtype=torch.float64, device=dev)
-
-    def step(kap, rhs, xout, marks=None):
-        # learned filter: the network's inference on this kappa is part of the step
-        if marks is not None:
-            marks.append([torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)])
-            marks[-1][0].record(stream)
-        t = net.forward(grid, kap, batch=1, t=t_buf) if net is not None else None
-        P = ffp.Preconditioner(grid, kap, bc, args.precision, precond=args.precond,
-                               workspace=work, t=t)
-        if marks is not None:
-            marks[-1][1].record(stream)
-        xout.zero_()
-        _, st = P.solve(rhs, x=xout, rtol=args.rtol, maxit=MAXIT, check=False)
-        P.close()
-        return st
+    step = solve_step(ffp, grid, bc, args.precision, args.precond, work, net, t_buf, args.rtol, stream)
 
     def barrier():
         if ws > 1:
             dist.barrier()
 
     for _ in range(args.warmup):
-        st = step(kappa, b, x)
+        step(kappa, b, x)
     torch.cuda.synchronize()
     # ---- device-resident timed region
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stats = []
-    marks = []  # CUDA events around each step's setup (filter inference included)
     barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            stats.append(step(kappa, b, x, marks))
-        e1.record(stream)
-        torch.cuda.synchronize()
+    ms, setup_ms, stats, clocks = timed_steps(step, kappa, b, x, args.steps, local)
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    setup_ms = sum(m0.elapsed_time(m1) for m0, m1 in marks) / len(marks)
     # ---- end to end through the public API with host buffers
+    e2e_steps = min(args.steps, args.e2e_steps)
     e2 = []
     barrier()
     torch.cuda.synchronize()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
@@ -256,11 +315,41 @@ def run_ours(args):
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev, ws)
     st = stats[-1]
     ok = all(s["status"] == 0 and s["rel_res_true"] < args.rtol for s in stats)
+
+    # ---- the plain FP64 form on the same GPU: FP64 factors, rowsum filter, same
+    # preconditioner and tolerance (one GPU only: the comparison the metric names)
+    fp64 = None
+    if args.fp64_steps > 0 and ws == 1 and not (args.precision == "fp64" and net is None):
+        del work
+        torch.cuda.empty_cache()
+        work64 = torch.empty(ffp.workspace_bytes(grid, "fp64"), dtype=torch.uint8, device=dev)
+        step64 = solve_step(ffp, grid, bc, "fp64", args.precond, work64, None, None, args.rtol, stream)
+        # warm-up: one setup and one preconditioner application load the FP64 kernels
+        P = ffp.Preconditioner(grid, kappa, bc, "fp64", precond=args.precond, workspace=work64)
+        P.apply(b)
+        P.close()
+        ms64, setup64, stats64, clocks64 = timed_steps(step64, kappa, b, x, args.fp64_steps, local)
+        s64 = stats64[-1]
+        fp64 = {"s": ms64 / 1e3, "setup_s": setup64 / 1e3, "iters": s64["iters"],
+                "rel_res_true": s64["rel_res_true"],
+                "converged": all(s["status"] == 0 and s["rel_res_true"] < args.rtol for s in stats64),
+                "steps": args.fp64_steps, "warmup": "one setup + one apply (loads the FP64 kernels)",
+                "ms_per_apply_ntd": s64["ntd_ms"] / max(s64["napply"], 1),
+                "clocks": clocks64}
+        del work64
+
     peak, peak_kind = load_peaks()
     ntd_per_apply_ms = st["ntd_ms"] / max(st["napply"], 1)
     algo_bytes = NTD_BYTES[args.precision] * n
     achieved = algo_bytes / (ntd_per_apply_ms * 1e-3) / 1e9 if ntd_per_apply_ms > 0 else None
     depth = (grid[2] + 1) * (grid[1] + 1)  # dependent line solves per apply
+    spmv_per_ms = st["spmv_ms"] / max(st["iters"], 1)
+    spmv_achieved = SPMV_BYTES * n / (spmv_per_ms * 1e-3) / 1e9 if spmv_per_ms > 0 else None
+    reasons = sorted(set(clocks.get("reasons", [])) | set((fp64 or {}).get("clocks", {}).get("reasons", [])))
+    clocks = dict(clocks, reasons=reasons)
+    filt = ("rowsum" if net is None else
+            "learned (conv net on log10 kappa, inference inside the step, weights "
+            + os.path.basename(args.weights) + ")")
     line = {
         "metric": METRIC,
         "value": ms / 1e3 / ws,          # seconds per solve for the whole job (N replicas in parallel)
@@ -279,8 +368,7 @@ def run_ours(args):
             "precond": {"combo": "B_c = NTD + ILU(0) (Sec. III Eq. (com))",
                         "ntd": "B_NTD (Sec. II)"}[args.precond],
             "factors": args.precision,
-            "filter": args.filter if args.filter == "rowsum" else
-            "learned (conv net on log10 kappa, weights " + os.path.basename(args.weights) + ")",
+            "filter": filt,
             "rtol": args.rtol,
             "setup_ms": setup_ms,
             "solve_ms": ms - setup_ms,
@@ -288,6 +376,8 @@ def run_ours(args):
             "iters_rec": st["iters_rec"],
             "rel_res_true": st["rel_res_true"],
             "converged": ok,
+            "fp64_rowsum": fp64,
+            "speedup_vs_fp64_rowsum": (fp64["s"] / (ms / 1e3)) if fp64 else None,
             "replicas": ws,
             "l2": (f"inputs larger than L2 (each FP64 vector {8 * n / 1e6:.0f} MB > 129 MB)" if 8 * n > L2_BYTES
                    else f"working set larger than L2 (workspace {wsb / 1e6:.0f} MB > 129 MB, each FP64 "
@@ -295,7 +385,7 @@ def run_ours(args):
                    f"fits in L2 (workspace {wsb / 1e6:.0f} MB): not a bench-grade timing"),
         },
         "roofline": {
-            "kernel": "apply_kernel (B_NTD sweeps)",
+            "kernel": "apply_kernel (B_NTD sweeps, 3 launches per apply)",
             "bound": "hbm",
             "achieved": achieved,
             "peak": peak,
@@ -303,20 +393,35 @@ def run_ours(args):
             "frac": (achieved / peak) if achieved else None,
             "peak_kind": peak_kind,
             "traffic": APPLY_TRAFFIC.get((args.workload, args.precision)),
+            "bytes_per_unknown": NTD_BYTES[args.precision],
             "algorithmic_bytes_per_apply": algo_bytes,
             "ms_per_apply": ntd_per_apply_ms,
+            "governing_bound": "dependency chain, not bandwidth: (nz+1)(ny+1) dependent line solves "
+                               "per apply; the time per line solve sets the apply's time",
             "dependent_line_solves_per_apply": depth,
             "ns_per_line_solve": ntd_per_apply_ms * 1e6 / depth,
         },
-        "e2e": {"value": e2e_ms / 1e3 / ws, "unit": "s",
+        "roofline_spmv": {
+            "kernel": "spmv_dot_kernel (q = A p fused with (p, q))",
+            "bound": "hbm",
+            "achieved": spmv_achieved,
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": (spmv_achieved / peak) if spmv_achieved else None,
+            "peak_kind": peak_kind,
+            "traffic": SPMV_TRAFFIC.get(args.workload),
+            "bytes_per_unknown": SPMV_BYTES,
+            "ms_per_launch": spmv_per_ms,
+        },
+        "e2e": {"value": e2e_ms / 1e3 / ws, "unit": "s", "steps": e2e_steps,
                 "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(sum(s["launches"] for s in stats))
         + args.steps * (ffp.setup_launches(grid, args.precond, user_t=net is not None)
                         + (6 if net is not None else 0)),
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, st["iters"], args.cpu_sample_iters)
+        line["cpu_baseline"] = cpu_baseline(w, args.workload, st["iters"], args.cpu_sample_iters)
     if ws > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -326,7 +431,10 @@ def run_ours(args):
 def run_batched(args):
     """The batched workload: every step sets up all 64 instances and solves
     all 256 (instance, right-hand side) pairs to rtol in one batch, launch
-    configuration from the autotuner (tuned once, in the first warm-up step)."""
+    configuration from the autotuner (tuned once, in the first warm-up step).
+    On N ranks the job is one list of 64 N instances (weak scaling), split by
+    lpt_partition on n; each rank sets up and solves its share as one batch,
+    with no collective on the data path."""
     import torch
     import torch.distributed as dist
     from paper_1909_09771_gb300 import ffp
@@ -338,7 +446,10 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     nrhs = 4
-    insts = I.workload_batched(seed=replica_seed("batched", args.seed, rank), nrhs=nrhs)
+    count = 64 * ws
+    all_grids = I.batched_grids(seed=args.seed, count=count)
+    mine = lpt_partition([int(np.prod(g)) for g in all_grids], ws)[rank]
+    insts = I.workload_batched(seed=args.seed, count=count, nrhs=nrhs, indices=mine)
     grids = [w["grid"] for w in insts]
     bcs = [w["bc"] for w in insts]
     ns = [int(np.prod(g)) for g in grids]
@@ -405,9 +516,14 @@ def run_batched(args):
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev, ws)
     stats, info = runs[-1]
     ok = all(s["status"] == 0 and s["rel_res_true"] < RTOL for st, _ in runs for s in st)
+    ok = bool(max_over_ranks([0.0 if ok else 1.0], dev, ws)[0] == 0.0)
+    stats = merge_pair_stats(stats, mine, nrhs, count, ws)
     iters = [s["iters"] for s in stats]
+    sizes = [int(np.prod(g)) for g in all_grids]
+    loads = [sum(sizes[i] for i in part) for part in lpt_partition(sizes, ws)]
     peak, peak_kind = load_peaks()
-    pair_unknowns = sum(ns[p // nrhs] for p in range(len(bs)))
+    pair_unknowns = sum(ns[p // nrhs] for p in range(len(bs)))   # this rank's
+    job_pair_unknowns = nrhs * sum(sizes)
     algo_bytes = NTD_BYTES[args.precision] * pair_unknowns
     ntd_ms = tuned.get("ntd_ms", 0.0)
     achieved = algo_bytes / (ntd_ms * 1e-3) / 1e9 if ntd_ms > 0 else None
@@ -431,9 +547,11 @@ def run_batched(args):
             "factors": args.precision,
             "filter": "rowsum",
             "rtol": RTOL,
-            "unknowns": sum(ns),
-            "pairs": len(bs),
-            "pair_unknowns_per_s": pair_unknowns / (ms / 1e3) * ws,
+            "unknowns": sum(sizes),
+            "pairs": len(stats),
+            "pair_unknowns_per_s": job_pair_unknowns / (ms / 1e3),
+            "sharding": (f"LPT on n = nx ny nz over {ws} ranks: {count} instances, loads "
+                         f"max/mean {max(loads) / (sum(loads) / ws):.3f}") if ws > 1 else "one rank",
             "iters_mean": float(np.mean(iters)),
             "iters_max": int(max(iters)),
             "converged": ok,
@@ -455,9 +573,10 @@ def run_batched(args):
             "ms_per_apply": ntd_ms,
         },
         "e2e": {"value": e2e_ms / 1e3 / ws, "unit": "s",
-                "h2d_bytes_per_step": 8 * (sum(ns) + pair_unknowns),
-                "d2h_bytes_per_step": 8 * pair_unknowns},
-        "gpu_launches": int(sum(st[0]["launches"] + inf["setup_launches"] for st, inf in runs)),
+                "h2d_bytes_per_step": 8 * (sum(sizes) + job_pair_unknowns),
+                "d2h_bytes_per_step": 8 * job_pair_unknowns},
+        "gpu_launches": int(max_over_ranks([sum(st[0]["launches"] + inf["setup_launches"]
+                                                for st, inf in runs)], dev, ws)[0]) * ws,
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -492,11 +611,23 @@ def cpu_baseline_batched(insts, iters, nrhs):
                       f"{len(insts)} setups and {len(iters)} solves ({sum(iters)} iterations)"}
 
 
-def cpu_baseline(w, iters, sample_iters):
+def oracle_iterations(workload):
+    """The oracle's own iteration count for a workload (B_c, FP64, rowsum,
+    rtol 1e-8), stored by oracle/reference_iterations.py, or None."""
+    p = os.path.join(ROOT, "oracle", "reference_iterations.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh)[workload]["iters"]
+    except Exception:
+        return None
+
+
+def cpu_baseline(w, workload, gpu_iters, sample_iters):
     """The oracle as it stands, one host core: assembly + setup + ILU(0) pivots
-    measured in full, plus `sample_iters` flexible-CG iterations with B_c; the
-    solve is extrapolated to `iters` iterations (the iteration count of the
-    same arithmetic).  Returns the line's cpu_baseline object."""
+    measured in full, plus `sample_iters` flexible-CG iterations with B_c
+    measured; the solve is extrapolated to the oracle's own iteration count
+    for this workload (stored by oracle/reference_iterations.py), or to the
+    GPU's count where none is stored.  Returns the line's cpu_baseline object."""
     from oracle import oracle as O
     g = w["grid"]
     t0 = time.perf_counter()
@@ -507,9 +638,15 @@ def cpu_baseline(w, iters, sample_iters):
     t0 = time.perf_counter()
     O.pcg(g, bands, f, w["b"], rtol=1e-300, maxit=sample_iters, flexible=True, ilu=D)
     t_iter = (time.perf_counter() - t0) / sample_iters
+    iters = oracle_iterations(workload)
+    src = "the oracle's own count, oracle/reference_iterations.json"
+    if iters is None:
+        iters, src = gpu_iters, "the GPU solve's count (no oracle count stored for this workload)"
     return {"value": t_setup + iters * t_iter, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"setup measured in full ({t_setup:.1f} s) + {sample_iters} B_c flexible-CG "
-                      f"iterations ({t_iter:.2f} s each), extrapolated to {iters} iterations"}
+            "extrapolated": True,
+            "sample": f"EXTRAPOLATED: setup measured in full ({t_setup:.1f} s) + {sample_iters} B_c "
+                      f"flexible-CG iterations measured ({t_iter:.2f} s each), times {iters} iterations "
+                      f"({src}); rowsum filter, FP64"}
 
 
 def run_reference(args):
@@ -519,11 +656,11 @@ def run_reference(args):
         return
     from oracle import oracle as O
     O.build()
-    iters = REFERENCE_ITERS.get(args.workload)
+    iters = oracle_iterations(args.workload)
     if args.workload == "batched":
         from paper_1909_09771_gb300 import inputs as I
         insts = I.workload_batched(seed=args.seed)
-        per_pair = [iters] * (4 * len(insts))
+        per_pair = [iters if iters else 1] * (4 * len(insts))
     else:
         w = make_workload(args.workload, seed=args.seed)
     times = []
@@ -531,7 +668,7 @@ def run_reference(args):
         if args.workload == "batched":
             cb = cpu_baseline_batched(insts, per_pair, 4)
         else:
-            cb = cpu_baseline(w, iters if iters else 1, 1)
+            cb = cpu_baseline(w, args.workload, 1, 1)
         if k >= args.warmup:
             times.append(cb["value"])
     v = sum(times) / len(times)
@@ -547,16 +684,11 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-# DRAM bytes of one B_NTD apply (the three sweep launches) from an ncu capture of
-# the current kernel (profiles/apply_traffic_grf350_fp32.md), by workload and factor
-# precision; absent = not measured for that kernel.
-APPLY_TRAFFIC = {("grf350", "fp32"): 2678.4e6}
-
-# Iterations B_c flexible CG takes to rtol 1e-8 on each workload (seed 0), as
-# counted by the library's FP64 solve, whose arithmetic matches the oracle's
-# (the parity tests hold the two iteration counts within one); for the batched
-# workload the mean over its 256 pairs (library, FP32 factors).
-REFERENCE_ITERS = {"grf350": 159, "blocks32": 22, "batched": 98}
+# DRAM bytes per launch from one ncu capture of the current kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum), by workload (and factor precision); absent = not measured for the
+# kernel as it now is.
+APPLY_TRAFFIC = {}
+SPMV_TRAFFIC = {}
 
 
 def main():
@@ -569,11 +701,14 @@ def main():
     ap.add_argument("--rtol", type=float, default=RTOL)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--precond", default="combo", choices=["combo", "ntd"])
-    ap.add_argument("--filter", default="rowsum", choices=["rowsum", "learned"])
+    ap.add_argument("--filter", default="learned", choices=["rowsum", "learned"])
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1909_09771_gb300",
                                                         "learned_filter_weights.txt"))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-sample-iters", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed solves of the plain FP64 rowsum form beside the main arm (0: none)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

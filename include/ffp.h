@@ -88,6 +88,8 @@ typedef struct {
     int iters_rec;        /* first iteration at which the recursive ||r|| / ||b|| fell below rtol
                              (-1 if it never did); iters can be larger when the true residual,
                              checked then, was not yet below rtol and the solve went on */
+    double spmv_ms;       /* device time of the iterations' q = A p launches (fused with
+                             (p, q)), CUDA events on `stream`; 0 in batched solves */
 } ffp_stats;
 
 typedef struct ffp_handle ffp_handle;
@@ -205,6 +207,22 @@ int ffp_export(ffp_handle *h, double *d, double *cx, double *cy, double *cz, dou
  * writes every scratch entry before reading it. */
 #define FFP_NOALLOC_MAX_PLANE 131072
 int ffp_apply_noalloc(ffp_handle *h, const double *r, double *z, void *stream);
+
+/* Test hook for the failure path (the paper has no counterpart).  Every wait
+ * inside the apply kernels -- a compute warp waiting for its producer to fill a
+ * shared-memory stage, a producer waiting for a stage to be released -- gives
+ * up after a fixed number of tries, records a timeout flag and lets the kernel
+ * run to its end, so a broken hand-off yields FFP_ERR_TIMEOUT from
+ * ffp_pcg_solve instead of a hung GPU.  This call lets a test exercise that
+ * path without faulting anything:
+ *   mode 1      in every following apply of this handle, one producer warp
+ *               of the first level-3 half withholds its first "stage full"
+ *               signal, so its compute warp's wait runs out (the apply's
+ *               result is then unusable); mode 0 restores normal operation
+ *   wait_tries  try limit of those waits while set (0 = the library default,
+ *               about 4 M tries); a small value makes the timeout quick
+ * Returns FFP_ERR_ARG for a null handle or an unknown mode. */
+int ffp_debug_stall(ffp_handle *h, int mode, unsigned wait_tries);
 
 /* Free the host handle (no device memory is freed). */
 void ffp_destroy(ffp_handle *h);

@@ -18,7 +18,8 @@ struct ffp_handle {
     KernelCtx c;
     int device;
     double *host_scal;  // pinned copy of the scalar block + flags
-    cudaEvent_t ev[4];  // preconditioner timing: start, B_NTD sweeps start and end, end
+    cudaEvent_t ev[6];  // preconditioner timing: start, B_NTD sweeps start and end, end;
+                        // then the start and end of the SpMV + (p, Ap) launch
 };
 
 const KernelCtx *ffp::handle_ctx(const ffp_handle *h) { return h ? &h->c : nullptr; }
@@ -173,7 +174,7 @@ int ffp_setup(const ffp_grid *grid, const double *kappa, const ffp_bc *bc, int f
     std::memset(h, 0, sizeof(*h));
     if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return FFP_ERR_CUDA; }
     if (cudaMallocHost((void **)&h->host_scal, kScalBytes) != cudaSuccess) { delete h; return FFP_ERR_CUDA; }
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 6; ++k)
         if (cudaEventCreate(&h->ev[k]) != cudaSuccess) { ffp_destroy(h); return FFP_ERR_CUDA; }
     KernelCtx &c = h->c;
     c.nx = grid->nx; c.ny = grid->ny; c.nz = grid->nz;
@@ -258,7 +259,7 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
     double best_true = -1.0;
     int stalls = 0;
     double bb = 0.0, rr = 0.0;
-    double pre_ms = 0.0, ntd_ms = 0.0;
+    double pre_ms = 0.0, ntd_ms = 0.0, spmv_ms = 0.0;
     long long nl = 0;
 #define FFP_TRY(expr)                                                 \
     do {                                                              \
@@ -302,7 +303,9 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
         FFP_TRY(launch_finalize(c, FIN_RZ, fresh, flexible, st));
         FFP_TRY(launch_update_p(c, fresh, st));
         fresh = 0;
+        FFP_TRY(cudaEventRecord(h->ev[4], st));
         FFP_TRY(launch_spmv_dot(c, st));
+        FFP_TRY(cudaEventRecord(h->ev[5], st));
         FFP_TRY(launch_finalize(c, FIN_PQ, 0, flexible, st));
         FFP_TRY(launch_update_xr(c, x, st));
         FFP_TRY(launch_finalize(c, FIN_RR, 0, flexible, st));
@@ -313,6 +316,8 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
             float a = 0.f, b2 = 0.f;
             if (cudaEventElapsedTime(&a, h->ev[0], h->ev[3]) == cudaSuccess) pre_ms += a;
             if (cudaEventElapsedTime(&b2, h->ev[1], h->ev[2]) == cudaSuccess) ntd_ms += b2;
+            float c2 = 0.f;
+            if (cudaEventElapsedTime(&c2, h->ev[4], h->ev[5]) == cudaSuccess) spmv_ms += c2;
         }
         if (host_flags(h)[FL_TIMEOUT]) { status = FFP_ERR_TIMEOUT; break; }
         if (host_flags(h)[FL_PQ]) { status = FFP_ERR_BREAKDOWN; break; }
@@ -326,6 +331,7 @@ done:
         stats->status = status;
         stats->precond_ms = pre_ms;
         stats->ntd_ms = ntd_ms;
+        stats->spmv_ms = spmv_ms;
         stats->napply = it;
         stats->rel_res = (bb > 0.0) ? std::sqrt(rr / bb) : 0.0;
         stats->rel_res_true = -1.0;
@@ -343,9 +349,16 @@ done:
     return status;
 }
 
+int ffp_debug_stall(ffp_handle *h, int mode, unsigned wait_tries) {
+    if (!h || mode < 0 || mode > 1) return FFP_ERR_ARG;
+    h->c.dbg_stall = mode;
+    h->c.dbg_tries = wait_tries;
+    return FFP_OK;
+}
+
 void ffp_destroy(ffp_handle *h) {
     if (!h) return;
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 6; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     if (h->host_scal) cudaFreeHost(h->host_scal);
     delete h;

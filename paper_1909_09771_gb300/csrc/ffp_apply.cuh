@@ -172,6 +172,8 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
     const ApplyArgs &src = table ? table[blockIdx.y] : A0;
     if (src.ctl && !(*src.ctl & 1)) return;  // a batched pair that does not iterate now
     const ApplyView<F> A(src);
+    const unsigned wtries = src.wait_tries;
+    const int stall = src.stall;
     using SG = Stage<S, F, PH>;
     constexpr int NF = SG::NF, NM = SG::NM, NV = SG::NV, NST = SG::NST, D = SG::D, VST = SG::VST;
     static_assert(SG::total(NST, VST, FFP_MAX_NX) <= kSmemBudget, "stage ring does not fit");
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
     auto issue_next = [&]() {
         if (fpl < npl && fg % kProducers == ppar) {
             const int slot = fg % NST, use = fg / NST;
-            if (use > 0 && !aborted && !mbar_wait(empty + slot, (use - 1) & 1)) {
+            if (use > 0 && !aborted && !mbar_wait(empty + slot, (use - 1) & 1, wtries)) {
                 aborted = true;
                 atomicOr(A.flags + FL_TIMEOUT, 1);
             }
@@ -321,7 +323,11 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
                     }
                 }
             }
-            mbar_arrive_cpasync(full + slot);
+            // the test hook withholds the first signal of one producer (the compute warp's
+            // wait then runs out; the kernel still ends, with unusable results)
+            const bool withhold = PH == 0 && stall == 1 && fg == 0 && wid == 0 && ppar == 0 &&
+                                  blockIdx.x == 0;
+            if (!withhold) mbar_arrive_cpasync(full + slot);
         }
         ++fg;
         if (++fs == spp) { fs = 0; ++fpl; }
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
     unsigned phase = 0;
     // wait until the current stage is full
     auto begin = [&]() -> const unsigned char * {
-        if (!aborted && !mbar_wait(full + slot, phase)) {
+        if (!aborted && !mbar_wait(full + slot, phase, wtries)) {
             aborted = true;
             atomicOr(A.flags + FL_TIMEOUT, 1);
         }
@@ -585,6 +591,8 @@ cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cuda
     a.scr = c.ws.ascr;
     a.flags = c.ws.flags;
     a.ctl = nullptr;
+    a.wait_tries = c.dbg_tries ? c.dbg_tries : kWaitTries;
+    a.stall = c.dbg_stall;
     a.r = c.ws.ra;
     a.z = c.ws.za;
     cudaError_t e = launch_to_lb(c, r, c.ws.ra, st);

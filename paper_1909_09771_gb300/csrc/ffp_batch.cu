@@ -559,6 +559,7 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
         c.ly = grids[i].ly > 0 ? grids[i].ly : 1.0;
         c.lz = grids[i].lz > 0 ? grids[i].lz : 1.0;
         c.prec = precision; c.precond = precond; c.slots = slots_for(c.nx);
+        c.dbg_stall = 0; c.dbg_tries = 0;
     }
     if (cudaMallocHost((void **)&B->hctl, 4 * (size_t)B->npairs) != cudaSuccess ||
         cudaMallocHost((void **)&B->hscal, kPairScal * (size_t)B->npairs) != cudaSuccess)
@@ -685,6 +686,8 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
         A.scr = ascr[up];
         A.flags = P.flags;
         A.ctl = P.ctl;
+        A.wait_tries = kWaitTries;
+        A.stall = 0;
         IluArgs &L = it[k];
         std::memset(&L, 0, sizeof(L));
         L.nx = c.nx; L.ny = c.ny; L.nz = c.nz;

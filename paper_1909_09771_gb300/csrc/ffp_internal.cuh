@@ -420,10 +420,12 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parit
     return ok != 0;
 }
 // Wait for a phase with an iteration limit: returns false (and the caller
-// records a timeout) if the phase does not complete in kWaitTries tries.
+// records a timeout) if the phase does not complete in `tries` tries
+// (kWaitTries unless a test lowers it).
 constexpr unsigned kWaitTries = 1u << 22;
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-    for (unsigned it = 0; it < kWaitTries; ++it)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          unsigned tries = kWaitTries) {
+    for (unsigned it = 0; it < tries; ++it)
         if (mbar_try(bar, parity)) return true;
     return false;
 }

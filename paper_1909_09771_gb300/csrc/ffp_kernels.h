@@ -16,6 +16,10 @@ struct KernelCtx {
     int precond;    // FFP_PRECOND_NTD / FFP_PRECOND_COMBO
     int slots;      // S of the line solver
     Ws ws;
+    // test hook (ffp_debug_stall): 1 = the apply withholds one stage signal;
+    // try limit of the apply's waits (0 = kWaitTries)
+    int dbg_stall;
+    unsigned dbg_tries;
 };
 
 // ffp_api.cu: bytes per stored factor value, and the workspace layout (base may
@@ -92,6 +96,9 @@ struct ApplyArgs {
     void *scr;        // 2 planes
     int *flags;
     const int *ctl;   // batched solves: the pair is skipped unless *ctl & 1 (null: always run)
+    unsigned wait_tries;  // try limit of every mbarrier wait (kWaitTries; lowered by a test)
+    int stall;        // test hook: 1 = the first producer of the first level-3 half withholds
+                      // its first "stage full" signal in phase 0, so a compute warp's wait runs out
 };
 
 // ffp_dispatch.cu: NTD apply of every pair of a device table (one launch per phase)

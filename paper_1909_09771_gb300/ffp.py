@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("rel_res_true", ctypes.c_double), ("solve_s", ctypes.c_double),
                 ("precond_ms", ctypes.c_double), ("ntd_ms", ctypes.c_double),
-                ("napply", ctypes.c_int), ("launches", ctypes.c_longlong), ("iters_rec", ctypes.c_int)]
+                ("napply", ctypes.c_int), ("launches", ctypes.c_longlong), ("iters_rec", ctypes.c_int),
+                ("spmv_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -102,6 +103,7 @@ def load():
     lib.ffp_strerror.argtypes = [ctypes.c_int]
     lib.ffp_strerror.restype = ctypes.c_char_p
     lib.ffp_apply_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.ffp_debug_stall.argtypes = [vp, ctypes.c_int, ctypes.c_uint]
     lib.ffp_batch_workspace_bytes.argtypes = [ctypes.c_int, P(Grid), ctypes.c_int, ctypes.c_int]
     lib.ffp_batch_workspace_bytes.restype = ctypes.c_size_t
     lib.ffp_batch_setup.argtypes = [ctypes.c_int, P(Grid), P(vp), P(BC), P(vp), ctypes.c_int,
@@ -129,7 +131,7 @@ def load():
     lib.ffp_filter_target.argtypes = [P(Grid), ctypes.c_int, P(ctypes.c_double), vp,
                                       ctypes.c_double, vp, vp, vp, ctypes.c_size_t, vp]
     for f in (lib.ffp_setup, lib.ffp_spmv, lib.ffp_apply, lib.ffp_pcg_solve, lib.ffp_export,
-              lib.ffp_apply_noalloc, lib.ffp_batch_setup, lib.ffp_batch_tune, lib.ffp_batch_get_config,
+              lib.ffp_apply_noalloc, lib.ffp_debug_stall, lib.ffp_batch_setup, lib.ffp_batch_tune, lib.ffp_batch_get_config,
               lib.ffp_batch_set_config, lib.ffp_batch_info, lib.ffp_batch_solve, lib.ffp_net_init,
               lib.ffp_net_cast, lib.ffp_net_forward, lib.ffp_net_grad, lib.ffp_net_adam,
               lib.ffp_lanczos_ritz, lib.ffp_filter_target):
@@ -264,12 +266,21 @@ class Preconditioner:
             raise FFPError(st, "ffp_pcg_solve")
         return x, s.as_dict()
 
-    def export(self, stream=None):
-        """Stored operator bands and factors as FP64 device tensors."""
-        names = ["d", "cx", "cy", "cz", "l3", "l2", "l1", "minv", "dinv"]
+    def debug_stall(self, mode, wait_tries=0):
+        """Test hook (ffp_debug_stall): mode 1 makes the following applies withhold
+        one stage signal so that a bounded wait runs out; mode 0 restores them."""
+        st = load().ffp_debug_stall(self._h, int(mode), int(wait_tries))
+        if st != FFP_OK:
+            raise FFPError(st, "ffp_debug_stall")
+
+    def export(self, names=None, stream=None):
+        """Stored operator bands and factors as FP64 device tensors: all of
+        d, cx, cy, cz, l3, l2, l1, minv, dinv, or the ones named."""
+        allnames = ["d", "cx", "cy", "cz", "l3", "l2", "l1", "minv", "dinv"]
+        names = allnames if names is None else list(names)
         out = {k: torch.empty(self.n, dtype=torch.float64, device=self.workspace.device)
                for k in names}
-        st = load().ffp_export(self._h, *[_ptr(out[k]) for k in names], _stream(stream))
+        st = load().ffp_export(self._h, *[_ptr(out.get(k)) for k in allnames], _stream(stream))
         if st != FFP_OK:
             raise FFPError(st, "ffp_export")
         return out

@@ -155,11 +155,19 @@ def workload_grf(seed=0, n=350, exponent=3.0):
     return dict(name=f"grf{n}", grid=grid, kappa=kappa, bc=BC_Z_DIRICHLET, b=b)
 
 
-def workload_batched(seed=0, count=64, nrhs=4, lo=48, hi=160):
+def batched_grids(seed=0, count=64, lo=48, hi=160):
+    """The grids of the batched workload's instances (the first draw of each
+    instance's generator), without generating their fields."""
+    return [tuple(int(v) for v in np.random.default_rng(seed + i).integers(lo, hi + 1, size=3))
+            for i in range(count)]
+
+
+def workload_batched(seed=0, count=64, nrhs=4, lo=48, hi=160, indices=None):
     """Instance i uses seed + i: sizes first, then its 8x8x8-block kappa, then
-    its nrhs right-hand sides."""
+    its nrhs right-hand sides.  indices: generate only these instances (in the
+    order given); default all `count`."""
     out = []
-    for i in range(count):
+    for i in (range(count) if indices is None else indices):
         rng = np.random.default_rng(seed + i)
         nx, ny, nz = (int(v) for v in rng.integers(lo, hi + 1, size=3))
         kappa = kappa_blocks((nx, ny, nz), 8, None, rng=rng)
