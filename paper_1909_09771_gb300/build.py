@@ -32,17 +32,25 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False,
+          profile: bool = False) -> str:
+    """Compile libffp.so (or, with profile=True, libffp_profile.so: the same
+    library with -DFFP_STEP_PROFILE, whose FP32 apply records a clock64 budget
+    of its line steps, read by ffp_step_profile(); see profile_steps.py).
+    Returns the library path."""
+    build_dir = BUILD + ("_profile" if profile else "")
+    lib_path = LIB.replace("libffp.so", "libffp_profile.so") if profile else LIB
+    extra = ["-DFFP_STEP_PROFILE"] if profile else []
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [
         os.path.join(HERE, "..", "include", "ffp.h")]
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         if force or _stale(o, [s] + hdrs):
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o]
+            cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append((src, cmd))
@@ -57,14 +65,14 @@ def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) 
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed on {src}")
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [os.path.join(build_dir, s.replace(".cu", ".o")) for s in SOURCES]
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    build(verbose=True, ptxas_info="-v" in sys.argv, force="-f" in sys.argv)
-    print(LIB)
+    print(build(verbose=True, ptxas_info="-v" in sys.argv, force="-f" in sys.argv,
+                profile="--profile" in sys.argv))

@@ -49,6 +49,24 @@
 
 namespace ffp {
 
+#ifdef FFP_STEP_PROFILE
+// Step profile (profiling builds only, see build.py --profile): clock64 stamps
+// around the segments of the line steps of compute warp 0 of the first CTA of
+// phase 0, accumulated by lane 0 and written out at the end of the launch.
+// Slots: lower steps [0] stage wait, [1] right-hand side, [2] line solve,
+// [3] store + release, [4] count; upper steps [5..9] likewise; [10] cycles of
+// the whole plane loop; [11] stage waits whose first try failed.
+static __device__ unsigned long long g_step_prof[16];
+__device__ __forceinline__ unsigned long long prof_stamp() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%clock64;" : "=l"(t)::"memory");
+    return t;
+}
+#define FFP_PROF(...) __VA_ARGS__
+#else
+#define FFP_PROF(...)
+#endif
+
 // Typed view of one (instance, right-hand side) pair's ApplyArgs.  Vectors are
 // in the compute type R: FP64 for FP64 factors, FP32 otherwise (the FP32 apply
 // converts r to FP32 and z back to FP64 in GPU-wide kernels around the
@@ -371,7 +389,9 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
     int slot = 0;
     unsigned phase = 0;
     // wait until the current stage is full
+    FFP_PROF(unsigned long long nfail = 0;)
     auto begin = [&]() -> const unsigned char * {
+        FFP_PROF(if (!mbar_try(full + slot, phase)) ++nfail;)
         if (!aborted && !mbar_wait(full + slot, phase, wtries)) {
             aborted = true;
             atomicOr(A.flags + FL_TIMEOUT, 1);
@@ -449,6 +469,9 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
         }
     };
 
+    FFP_PROF(const bool prof = PH == 0 && blockIdx.x == 0 && blockIdx.y == 0 && wid == 0 && lane == 0;
+             unsigned long long pacc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+             const unsigned long long pstart = prof_stamp();)
     for (int pl = 0; pl < npl; ++pl) {
         int i, other, cpl;
         plane_of(pl, i, other, cpl);
@@ -461,7 +484,9 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
         // steps t < TN read the coupled plane's row directly (written fewer than NST steps ago)
         constexpr int TN = (D + 1) / 2;
         auto lower = [&](int t, bool near) {
+            FFP_PROF(const unsigned long long p0 = prof_stamp();)
             const unsigned char *st = begin();
+            FFP_PROF(const unsigned long long p1 = prof_stamp();)
             const int k = line_of(t);
             const long bk = pblk + (long)k * BL;
             R b[S], bm;
@@ -474,12 +499,17 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
                 bm -= M_(st, 1, MID_L2) * wm;
             }
             R x[S], xm;
+            FFP_PROF(const unsigned long long p2 = prof_stamp();)
             solve(st, b, bm, x, xm);
+            FFP_PROF(const unsigned long long p3 = prof_stamp();)
             put((PH == 2) ? scrp + (long)k * BL : A.z + bk, x, xm);
 #pragma unroll
             for (int s = 0; s < S; ++s) w[s] = x[s];
             wm = xm;
             finish();
+            FFP_PROF(if (prof) { const unsigned long long p4 = prof_stamp();
+                                 pacc[0] += p1 - p0; pacc[1] += p2 - p1; pacc[2] += p3 - p2;
+                                 pacc[3] += p4 - p3; pacc[4] += 1; })
         };
         {
             int t = 0;
@@ -528,7 +558,9 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
         // ------------------------------------------------------------ upper sweep
         // the first D/2 steps read the lower-sweep row directly (written < NST steps ago)
         auto upper = [&](int t, bool near) {
+            FFP_PROF(const unsigned long long p0 = prof_stamp();)
             const unsigned char *st = begin();
+            FFP_PROF(const unsigned long long p1 = prof_stamp();)
             const int k = line_of(t);
             const long bk = pblk + (long)k * BL;
             R l2[S], b[S], bm;
@@ -537,7 +569,9 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
             for (int s = 0; s < S; ++s) b[s] = l2[s] * u[s];
             bm = M_(st, 1, MID_L2) * um;
             R x[S], xm;
+            FFP_PROF(const unsigned long long p2 = prof_stamp();)
             solve(st, b, bm, x, xm);
+            FFP_PROF(const unsigned long long p3 = prof_stamp();)
             R wv[S], wvm;
             if (VST && !near) ldrow(Vp(st, 0), wv, wvm);
             else ldrow((PH == 2) ? scrp + (long)k * BL : A.z + bk, wv, wvm);
@@ -558,6 +592,9 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
             }
             put(A.z + bk, f, fm);
             finish();
+            FFP_PROF(if (prof) { const unsigned long long p4 = prof_stamp();
+                                 pacc[5] += p1 - p0; pacc[6] += p2 - p1; pacc[7] += p3 - p2;
+                                 pacc[8] += p4 - p3; pacc[9] += 1; })
         };
         {
             int t = nl - 1;
@@ -565,7 +602,18 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
             for (; t >= 0; --t) upper(t, false);
         }
     }
+    FFP_PROF(if (prof) {
+        for (int q = 0; q < 10; ++q) g_step_prof[q] = pacc[q];
+        g_step_prof[10] = prof_stamp() - pstart;
+        g_step_prof[11] = nfail;
+    })
 }
+
+#ifdef FFP_STEP_PROFILE
+inline cudaError_t step_profile_read(unsigned long long *host) {
+    return cudaMemcpyFromSymbol(host, g_step_prof, sizeof(g_step_prof));
+}
+#endif
 
 template <int S, typename F, int PH>
 static cudaError_t launch_phase(const ApplyArgs &a, const ApplyArgs *table, int nx_max, dim3 grid,

@@ -8,3 +8,11 @@ namespace ffp {
 FFP_SLOT_LIST(FFP_INST)
 #undef FFP_INST
 }  // namespace ffp
+
+#ifdef FFP_STEP_PROFILE
+// Profiling builds only (build.py --profile; not part of include/ffp.h): the
+// step profile of the last FP32-factor apply, 16 counters (see g_step_prof).
+extern "C" int ffp_step_profile(unsigned long long *host16) {
+    return ffp::step_profile_read(host16) == cudaSuccess ? 0 : -2;
+}
+#endif
