@@ -211,7 +211,7 @@ def max_over_ranks(values, device, world_size):
     return [float(v) for v in t.tolist()]
 
 
-def solve_step(ffp, grid, bc, precision, precond, work, net, t_buf, rtol, stream):
+def solve_step(ffp, grid, bc, precision, precond, work, net, t_buf, rtol, stream, schur="newton"):
     """One pass of the hot path on resident inputs: the learned filter's
     inference (if any), assembly + setup, and the flexible-CG solve to rtol.
     Returns a function step(kappa, b, x, marks) -> stats."""
@@ -222,7 +222,8 @@ def solve_step(ffp, grid, bc, precision, precond, work, net, t_buf, rtol, stream
             marks.append([torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)])
             marks[-1][0].record(stream)
         t = net.forward(grid, kap, batch=1, t=t_buf) if net is not None else None
-        P = ffp.Preconditioner(grid, kap, bc, precision, precond=precond, workspace=work, t=t)
+        P = ffp.Preconditioner(grid, kap, bc, precision, precond=precond, workspace=work, t=t,
+                               schur=schur)
         if marks is not None:
             marks[-1][1].record(stream)
         xout.zero_()
@@ -281,7 +282,8 @@ def run_ours(args):
         from paper_1909_09771_gb300 import learned as LF
         net = LF.load_weights(args.weights, device=dev)
         t_buf = torch.empty(n, dtype=torch.float64, device=dev)
-    step = solve_step(ffp, grid, bc, args.precision, args.precond, work, net, t_buf, args.rtol, stream)
+    step = solve_step(ffp, grid, bc, args.precision, args.precond, work, net, t_buf, args.rtol, stream,
+                      args.schur)
 
     def barrier():
         if ws > 1:
@@ -323,9 +325,11 @@ def run_ours(args):
         del work
         torch.cuda.empty_cache()
         work64 = torch.empty(ffp.workspace_bytes(grid, "fp64"), dtype=torch.uint8, device=dev)
-        step64 = solve_step(ffp, grid, bc, "fp64", args.precond, work64, None, None, args.rtol, stream)
+        step64 = solve_step(ffp, grid, bc, "fp64", args.precond, work64, None, None, args.rtol, stream,
+                            args.schur)
         # warm-up: one setup and one preconditioner application load the FP64 kernels
-        P = ffp.Preconditioner(grid, kappa, bc, "fp64", precond=args.precond, workspace=work64)
+        P = ffp.Preconditioner(grid, kappa, bc, "fp64", precond=args.precond, workspace=work64,
+                               schur=args.schur)
         P.apply(b)
         P.close()
         ms64, setup64, stats64, clocks64 = timed_steps(step64, kappa, b, x, args.fp64_steps, local)
@@ -368,6 +372,8 @@ def run_ours(args):
             "precond": {"combo": "B_c = NTD + ILU(0) (Sec. III Eq. (com))",
                         "ntd": "B_NTD (Sec. II)"}[args.precond],
             "factors": args.precision,
+            "schur": {"newton": "X = 2 beta - beta P beta (Sec. II-A as printed)",
+                      "beta": "X = beta (classical filtering; FFP_SCHUR_BETA)"}[args.schur],
             "filter": filt,
             "rtol": args.rtol,
             "setup_ms": setup_ms,
@@ -701,6 +707,9 @@ def main():
     ap.add_argument("--rtol", type=float, default=RTOL)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--precond", default="combo", choices=["combo", "ntd"])
+    ap.add_argument("--schur", default="newton", choices=["newton", "beta"],
+                    help="approximate inverse in the Schur terms: newton = 2 beta - beta P beta "
+                         "(Sec. II-A as printed), beta = the classical X = beta")
     ap.add_argument("--filter", default="learned", choices=["rowsum", "learned"])
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1909_09771_gb300",
                                                         "learned_filter_weights.txt"))

@@ -57,6 +57,15 @@ extern "C" {
                                        ILU(0) of blkD(A) split at M = floor(N/2) (Sec. III, Eq. (com)),
                                        the preconditioner of the paper's experiments */
 
+/* Option OR'ed into `precond`: the approximate inverse X of the eliminated
+ * block in the Schur terms of the plane and line recurrences (Sec. II-A).  By
+ * default X = 2 beta - beta P beta, the form the recurrences print, which the
+ * paper presents as an improvement on beta alone.  With FFP_SCHUR_BETA,
+ * X = beta = diag((P^{-1} w) ./ w), the classical filtering approximation: the
+ * Schur terms then change only the diagonals of P_i and T_k, and the filtering
+ * property X w = P^{-1} w holds all the same. */
+#define FFP_SCHUR_BETA 16
+
 /* storage and arithmetic precision of the preconditioner factors */
 #define FFP_FP64 0                  /* FP64 factors, FP64 apply, standard PCG (flexible CG with B_c) */
 #define FFP_FP32 1                  /* FP32 factors, FP32 apply, FP64 flexible CG */
@@ -123,7 +132,7 @@ size_t ffp_workspace_bytes(const ffp_grid *grid, int precision);
  *   filter     FFP_FILTER_ROWSUM (t ignored, may be NULL) or FFP_FILTER_USER
  *   t          device FP64 [N] filter vector (entries > 0, else FFP_ERR_ARG)
  *   precision  FFP_FP64, FFP_FP32 or FFP_BF16
- *   precond    FFP_PRECOND_NTD or FFP_PRECOND_COMBO
+ *   precond    FFP_PRECOND_NTD or FFP_PRECOND_COMBO, optionally | FFP_SCHUR_BETA
  *   workspace  device memory of ws_bytes >= ffp_workspace_bytes(grid, precision),
  *              owned by the caller and kept alive until ffp_destroy
  *   out        receives a host handle (freed by ffp_destroy)

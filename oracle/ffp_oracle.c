@@ -133,6 +133,7 @@ typedef struct {
     int nx, ny, nz;
     const double *l[4]; /* l[1]=l1 (x-band of T), l[2]=l2 (y-band of P), l[3]=l3 (z-band of A) */
     const double *M;    /* level-1 twisted pivots */
+    int classic;        /* setup only: X = beta in the Schur terms instead of 2 beta - beta P beta */
 } ntd_ctx;
 
 static long block_size(const ntd_ctx *c, int level)
@@ -236,6 +237,7 @@ int or_apply(int nx, int ny, int nz, const double *l3, const double *l2, const d
     c.nx = nx; c.ny = ny; c.nz = nz;
     c.l[0] = NULL; c.l[1] = l1; c.l[2] = l2; c.l[3] = l3;
     c.M = M;
+    c.classic = 0;
     const long n = (long)nx * ny * nz;
     ntd_solve(&c, 0, n, 3, r, z);     /* SOLVE(1, N, x, y, n^2, 3) */
     return OR_OK;
@@ -298,11 +300,13 @@ static void line_schur(const ntd_ctx *c, int nx, long ls, const double *Td, cons
     for (int a = 0; a < nx; ++a) w[a] = p[a] * (t ? t[a] : 1.0);
     solve_block(c, ls, 1, w - ls, v - ls);                 /* v = T_s^{-1} w (exact) */
     for (int a = 0; a < nx; ++a) beta[a] = beta_of(v[a], w[a], Td[ls + a]);
-    /* X = 2 beta - beta T_s beta  (tridiagonal) ; Schur term = -p X p */
+    /* X = 2 beta - beta T_s beta  (tridiagonal) ; Schur term = -p X p.  With
+     * c->classic, X = beta (diagonal), the approximation the recurrences'
+     * 2 beta - beta T beta is presented as improving on. */
     for (int a = 0; a < nx; ++a) {
         const double xd = 2.0 * beta[a] - beta[a] * Td[ls + a] * beta[a];
-        dk[a] -= p[a] * xd * p[a];
-        if (a + 1 < nx) {
+        dk[a] -= p[a] * (c->classic ? beta[a] : xd) * p[a];
+        if (a + 1 < nx && !c->classic) {
             const double xo = -beta[a] * To[ls + a] * beta[a + 1];
             ok[a] -= p[a] * xo * p[a + 1];
         }
@@ -379,7 +383,8 @@ static void plane_schur(const ntd_ctx *c, long ps, const double *Pd, const doubl
     for (long e = 0; e < nxy; ++e) {
         const int ix = (int)(e % nx), iy = (int)(e / nx);
         const double xd = 2.0 * beta[e] - beta[e] * Pd[ps + e] * beta[e];
-        dk[e] -= C[e] * xd * C[e];
+        dk[e] -= C[e] * (c->classic ? beta[e] : xd) * C[e];
+        if (c->classic) continue;                         /* X = beta: diagonal only */
         if (ix + 1 < nx) {
             const double xo = -beta[e] * Px[ps + e] * beta[e + 1];
             xk[e] -= C[e] * xo * C[e + 1];
@@ -392,7 +397,7 @@ static void plane_schur(const ntd_ctx *c, long ps, const double *Pd, const doubl
 }
 
 int or_setup(int nx, int ny, int nz, const double *d, const double *cx, const double *cy,
-             const double *cz, const double *t,
+             const double *cz, const double *t, int classic,
              double *Pd, double *Px, double *Py, double *Td, double *To, double *M)
 {
     if (nx < 1 || ny < 1 || nz < 1) return OR_ERR_ARG;
@@ -404,6 +409,7 @@ int or_setup(int nx, int ny, int nz, const double *d, const double *cx, const do
     c.nx = nx; c.ny = ny; c.nz = nz;
     c.l[0] = NULL; c.l[1] = To; c.l[2] = Py; c.l[3] = cz;
     c.M = M;
+    c.classic = classic ? 1 : 0;
     double *w = (double *)malloc(sizeof(double) * nxy * 3);
     if (!w) return OR_ERR_ALLOC;
     double *v = w + nxy, *beta = w + 2 * nxy;

@@ -13,8 +13,10 @@ int or_assemble(int nx, int ny, int nz, double lx, double ly, double lz,
                 double *d, double *cx, double *cy, double *cz);
 int or_spmv(int nx, int ny, int nz, const double *d, const double *cx, const double *cy,
             const double *cz, const double *x, double *y);
+/* classic = 0: the Schur terms use X = 2 beta - beta P beta (Sec. II-A as
+ * printed); classic = 1: X = beta. */
 int or_setup(int nx, int ny, int nz, const double *d, const double *cx, const double *cy,
-             const double *cz, const double *t,
+             const double *cz, const double *t, int classic,
              double *Pd, double *Px, double *Py, double *Td, double *To, double *M);
 int or_apply(int nx, int ny, int nz, const double *l3, const double *l2, const double *l1,
              const double *M, const double *r, double *z);

@@ -52,7 +52,7 @@ def _load():
             i, d = ctypes.c_int, ctypes.c_double
             lib.or_assemble.argtypes = [i, i, i, d, d, d, _D, ctypes.c_char_p, _D, _D, _D, _D]
             lib.or_spmv.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D]
-            lib.or_setup.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+            lib.or_setup.argtypes = [i, i, i, _D, _D, _D, _D, _D, i, _D, _D, _D, _D, _D, _D]
             lib.or_apply.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D]
             lib.or_pcg.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, d, i, i,
                                    ctypes.POINTER(i), ctypes.POINTER(d), _D, _D, _D]
@@ -122,14 +122,16 @@ class Factors:
         return self.To
 
 
-def setup(grid, bands, t=None):
+def setup(grid, bands, t=None, schur="newton"):
+    """schur: "newton" -- X = 2 beta - beta P beta in the Schur terms (Sec. II-A as
+    printed); "beta" -- X = beta (classical filtering)."""
     nx, ny, nz = grid
     n = nx * ny * nz
     d, cx, cy, cz = bands
     outs = [np.empty(n) for _ in range(6)]
     tt = None if t is None else np.ascontiguousarray(t, dtype=np.float64).reshape(-1)
     _check(_load().or_setup(nx, ny, nz, _p(d), _p(cx), _p(cy), _p(cz), _p(tt),
-                            *[_p(o) for o in outs]), "or_setup")
+                            {"newton": 0, "beta": 1}[schur], *[_p(o) for o in outs]), "or_setup")
     return Factors(grid, cz, *outs)
 
 

@@ -158,6 +158,8 @@ int ffp_setup(const ffp_grid *grid, const double *kappa, const ffp_bc *bc, int f
     if (!grid_ok(grid) || !kappa || !bc || !workspace || !out) return FFP_ERR_ARG;
     if (prec_bytes(precision) == 0) return FFP_ERR_ARG;
     if (filter != FFP_FILTER_ROWSUM && filter != FFP_FILTER_USER) return FFP_ERR_ARG;
+    const int schur = (precond & FFP_SCHUR_BETA) ? 1 : 0;
+    precond &= ~FFP_SCHUR_BETA;
     if (precond != FFP_PRECOND_NTD && precond != FFP_PRECOND_COMBO) return FFP_ERR_ARG;
     if (filter == FFP_FILTER_USER && !t) return FFP_ERR_ARG;
     if (((uintptr_t)workspace & 255) != 0) return FFP_ERR_ARG;
@@ -184,6 +186,7 @@ int ffp_setup(const ffp_grid *grid, const double *kappa, const ffp_bc *bc, int f
     c.lz = grid->lz > 0 ? grid->lz : 1.0;
     c.prec = precision;
     c.precond = precond;
+    c.schur = schur;
     c.slots = slots;
     carve(grid, precision, (char *)workspace, &c.ws);
 

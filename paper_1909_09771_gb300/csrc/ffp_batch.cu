@@ -520,6 +520,8 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
     if (out) *out = nullptr;
     if (count < 1 || nrhs < 1 || !grids || !kappa || !bcs || !workspace || !out) return FFP_ERR_ARG;
     if (prec_bytes(precision) == 0) return FFP_ERR_ARG;
+    const int schur = (precond & FFP_SCHUR_BETA) ? 1 : 0;
+    precond &= ~FFP_SCHUR_BETA;
     if (precond != FFP_PRECOND_NTD && precond != FFP_PRECOND_COMBO) return FFP_ERR_ARG;
     if (((uintptr_t)workspace & 255) != 0) return FFP_ERR_ARG;
     for (int i = 0; i < count; ++i) {
@@ -558,7 +560,7 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
         c.lx = grids[i].lx > 0 ? grids[i].lx : 1.0;
         c.ly = grids[i].ly > 0 ? grids[i].ly : 1.0;
         c.lz = grids[i].lz > 0 ? grids[i].lz : 1.0;
-        c.prec = precision; c.precond = precond; c.slots = slots_for(c.nx);
+        c.prec = precision; c.precond = precond; c.schur = schur; c.slots = slots_for(c.nx);
         c.dbg_stall = 0; c.dbg_tries = 0;
     }
     if (cudaMallocHost((void **)&B->hctl, 4 * (size_t)B->npairs) != cudaSuccess ||

@@ -15,6 +15,7 @@ struct KernelCtx {
     int prec;       // FFP_FP64 / FFP_FP32 / FFP_BF16
     int precond;    // FFP_PRECOND_NTD / FFP_PRECOND_COMBO
     int slots;      // S of the line solver
+    int schur;      // approximate inverse in the Schur terms: 0 = 2 beta - beta P beta, 1 = beta
     Ws ws;
     // test hook (ffp_debug_stall): 1 = the apply withholds one stage signal;
     // try limit of the apply's waits (0 = kWaitTries)
@@ -64,6 +65,7 @@ cudaError_t launch_setup(const KernelCtx &c, const double *t, cudaStream_t st);
 struct SetupArgs {
     int nx, ny, nz;
     int prec;  // storage precision of the factor records
+    int schur; // 0: X = 2 beta - beta P beta (Sec. II-A as printed); 1: X = beta
     const double *d, *cx, *cy, *cz;
     const double *t;  // filter, NULL = rowsum
     void *rec;        // factor line records (rec_len(S) entries per line)
@@ -72,7 +74,7 @@ struct SetupArgs {
 };
 
 inline void fill_setup_args(const KernelCtx &c, const double *t, SetupArgs *a) {
-    a->nx = c.nx; a->ny = c.ny; a->nz = c.nz; a->prec = c.prec;
+    a->nx = c.nx; a->ny = c.ny; a->nz = c.nz; a->prec = c.prec; a->schur = c.schur;
     a->d = c.ws.d; a->cx = c.ws.cx; a->cy = c.ws.cy; a->cz = c.ws.cz;
     a->t = t;
     a->rec = c.ws.rec;

@@ -152,7 +152,7 @@ __device__ __forceinline__ void line_schur(const LineMap &L, int nx, int lane, i
                                            const LineState<S> &st, const double *p,
                                            const double *tl, double *SB, double *SP,
                                            double (&cd)[S], double (&co)[S], double &cdm,
-                                           double &com, SlotSplit &sp) {
+                                           double &com, SlotSplit &sp, int classic) {
     double w[S], wm, pa[S], pm;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -190,18 +190,18 @@ __device__ __forceinline__ void line_schur(const LineMap &L, int nx, int lane, i
         cd[s] = 0.0; co[s] = 0.0;
         if (sp.mine(s) && s < cnt) {
             const int a = slot_cell<S>(L, lane, s);
-            const double xd = 2.0 * be[s] - be[s] * st.Td[s] * be[s];
+            const double xd = classic ? be[s] : 2.0 * be[s] - be[s] * st.Td[s] * be[s];
             cd[s] = pa[s] * xd * pa[s];
-            if (a + 1 < nx) {
+            if (a + 1 < nx && !classic) {
                 const double xo = -be[s] * st.To[s] * SB[a + 1];
                 co[s] = pa[s] * xo * SP[a + 1];
             }
         }
     }
     {
-        const double xd = 2.0 * bem - bem * st.Tdm * bem;
+        const double xd = classic ? bem : 2.0 * bem - bem * st.Tdm * bem;
         cdm = pm * xd * pm;
-        if (L.m + 1 < nx) {
+        if (L.m + 1 < nx && !classic) {
             const double xo = -bem * st.Tom * SB[L.m + 1];
             com = pm * xo * SP[L.m + 1];
         } else {
@@ -293,7 +293,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
                              const double *Px, const double *Py, const double *tp, double *l1d,
                              double *mid, void *rec, void *l1n, long line0, int prec,
                              double *lbuf, double *meet, int wid, int lane, int cnt,
-                             int *flags, SlotSplit &sp) {
+                             int *flags, SlotSplit &sp, int classic) {
     const int my = (ny - 1) / 2;
     const int nl = (wid == 0) ? my : ny - 1 - my;
     double *SB = lbuf + wid * 3 * nx, *SP = SB + nx, *SO = SP + nx;
@@ -316,7 +316,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
         if (t > 0) {
             const int kc = (wid == 0) ? k - 1 : k;
             line_schur<S>(L, nx, lane, cnt, st, Py + (long)kc * nx, tp ? tp + o : nullptr, SB, SP,
-                          cd, co, cdm, com, sp);
+                          cd, co, cdm, com, sp, classic);
 #pragma unroll
             for (int s = 0; s < S; ++s)
                 if (sp.mine(s)) { Td[s] -= cd[s]; To[s] -= co[s]; }
@@ -332,7 +332,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
         const int kc = (wid == 0) ? my - 1 : my;
         if (nl > 0) {
             line_schur<S>(L, nx, lane, cnt, st, Py + (long)kc * nx, tp ? tp + o : nullptr, SB, SP,
-                          cd, co, cdm, com, sp);
+                          cd, co, cdm, com, sp, classic);
         } else {
 #pragma unroll
             for (int s = 0; s < S; ++s) { cd[s] = 0.0; co[s] = 0.0; }
@@ -402,7 +402,7 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
             if (wid < 4)
                 level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + i * nxy : nullptr, l1d, mid,
                                 A.rec, A.l1n, (long)i * ny, A.prec, lbuf, meet, half, lane, cnt,
-                                flags, sp);
+                                flags, sp, A.schur);
             const int dst = (t == nl3 - 1) ? mz : ((h == 0) ? i + 1 : i - 1);
             const int ic = (i < dst) ? i : dst;
             const double *C = A.cz + ic * nxy;
@@ -427,14 +427,14 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
             for (long e = tid; e < nxy; e += blockDim.x) {
                 const int ix = (int)(e % nx), iy = (int)(e / nx);
                 const double be = V[e];
-                const double xd = 2.0 * be - be * Pd[e] * be;
+                const double xd = A.schur ? be : 2.0 * be - be * Pd[e] * be;
                 const double cd = C[e] * xd * C[e];
                 double cxo = 0.0, cyo = 0.0;
-                if (ix + 1 < nx) {
+                if (ix + 1 < nx && !A.schur) {
                     const double xo = -be * Px[e] * V[e + 1];
                     cxo = C[e] * xo * C[e + 1];
                 }
-                if (iy + 1 < ny) {
+                if (iy + 1 < ny && !A.schur) {
                     const double xo = -be * Py[e] * V[e + nx];
                     cyo = C[e] * xo * C[e + nx];
                 }
@@ -465,7 +465,7 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
         if (wid < 4)
             level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + g0 : nullptr, A.ws.sF[0][0],
                             A.ws.sF[0][1], A.rec, A.l1n, (long)mz * ny, A.prec, lbuf, meet, half,
-                            lane, cnt, flags, sp);
+                            lane, cnt, flags, sp, A.schur);
     }
 }
 

@@ -30,8 +30,10 @@ FFP_DIRICHLET, FFP_NEUMANN = 0, 1
 FFP_FILTER_ROWSUM, FFP_FILTER_USER = 0, 1
 FFP_FP64, FFP_FP32, FFP_BF16 = 0, 1, 2
 FFP_PRECOND_NTD, FFP_PRECOND_COMBO = 0, 1
+FFP_SCHUR_BETA = 16
 PRECISIONS = {"fp64": FFP_FP64, "fp32": FFP_FP32, "bf16": FFP_BF16}
 PRECONDS = {"ntd": FFP_PRECOND_NTD, "combo": FFP_PRECOND_COMBO}
+SCHURS = {"newton": 0, "beta": FFP_SCHUR_BETA}
 
 
 class Grid(ctypes.Structure):
@@ -190,7 +192,9 @@ class Preconditioner:
     this object; the library only points into it."""
 
     def __init__(self, grid, kappa, bc, precision="fp64", t=None, lengths=(1.0, 1.0, 1.0),
-                 stream=None, precond="ntd", workspace=None):
+                 stream=None, precond="ntd", workspace=None, schur="newton"):
+        """schur: "newton" (X = 2 beta - beta P beta, Sec. II-A as printed) or
+        "beta" (X = beta, FFP_SCHUR_BETA)."""
         lib = load()
         self.grid = tuple(int(v) for v in grid)
         self.n = self.grid[0] * self.grid[1] * self.grid[2]
@@ -215,7 +219,7 @@ class Preconditioner:
         h = ctypes.c_void_p()
         st = lib.ffp_setup(ctypes.byref(g), _ptr(kappa), ctypes.byref(b),
                            FFP_FILTER_USER if t is not None else FFP_FILTER_ROWSUM, _ptr(t),
-                           PRECISIONS[precision], PRECONDS[precond], _ptr(self.workspace),
+                           PRECISIONS[precision], PRECONDS[precond] | SCHURS[schur], _ptr(self.workspace),
                            ctypes.c_size_t(nbytes),
                            _stream(stream), ctypes.byref(h))
         if st != FFP_OK:
@@ -305,7 +309,7 @@ class Batch:
     (ffp_batch_* in include/ffp.h).  Pairs are numbered i * nrhs + j."""
 
     def __init__(self, grids, kappas, bcs, nrhs=1, precision="fp32", precond="combo", ts=None,
-                 lengths=None, stream=None, workspace=None):
+                 lengths=None, stream=None, workspace=None, schur="newton"):
         lib = load()
         self.grids = [tuple(int(v) for v in g) for g in grids]
         self.count = len(self.grids)
@@ -333,7 +337,8 @@ class Batch:
         h = ctypes.c_void_p()
         st = lib.ffp_batch_setup(self.count, self._g, _ptr_array(kappas), bca,
                                  _ptr_array(ts) if ts is not None else None, self.nrhs,
-                                 PRECISIONS[precision], PRECONDS[precond], _ptr(self.workspace),
+                                 PRECISIONS[precision], PRECONDS[precond] | SCHURS[schur],
+                                 _ptr(self.workspace),
                                  ctypes.c_size_t(nbytes), _stream(stream), ctypes.byref(h))
         if st != FFP_OK:
             raise FFPError(st, "ffp_batch_setup")

@@ -42,13 +42,13 @@ def apply_scale(f, r):
     return s, z
 
 
-def sensitivity(grid, bands, f, r, s, seed=99, t=None):
+def sensitivity(grid, bands, f, r, s, seed=99, t=None, schur="newton"):
     """(kappa_factors, amp_apply): the oracle's relative change of the factors
     (l2, l1, 1/M; max per entry) and of the apply (max per entry over s) when
     every band moves by a random relative PERTURB, each divided by PERTURB."""
     rng = np.random.default_rng(seed)
     bp = tuple(b * (1.0 + PERTURB * rng.uniform(-1.0, 1.0, b.size)) for b in bands)
-    fp = o.setup(grid, bp, t)
+    fp = o.setup(grid, bp, t, schur=schur)
 
     def rel(a, b):
         return float(np.max(np.abs(a - b) / (np.abs(b) + 1e-300)))

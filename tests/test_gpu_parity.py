@@ -379,3 +379,59 @@ def test_unreachable_tolerance_stops_early(precision):
     assert st["status"] == ffp.FFP_ERR_NOT_CONVERGED
     assert 0 < st["iters_rec"] < st["iters"] < 600
     assert st["rel_res_true"] < 1e-12
+
+
+# ---------------------------------------------------------------- X = beta (FFP_SCHUR_BETA)
+SCHUR_GRIDS = [(1, 1, 5), (5, 6, 7), (33, 5, 4), (17, 3, 9), (64, 8, 6), (350, 3, 4), (70, 24, 20)]
+
+
+@pytest.mark.parametrize("grid", SCHUR_GRIDS)
+def test_schur_beta_setup_and_apply_parity_fp64(grid):
+    """The classical Schur form X = beta: stored factors per entry within the
+    derived bound, the apply kernel on the GPU's own factors (1e-12 per entry
+    of s) and setup + apply end to end against the oracle's X = beta form."""
+    w = I.random_small(grid, 61, contrast_exp=3)
+    P = ffp.Preconditioner(grid, dev(w["kappa"]), w["bc"], "fp64", schur="beta")
+    bands = o.assemble(grid, w["kappa"], w["bc"])
+    f = o.setup(grid, bands, schur="beta")
+    r = np.random.default_rng(62).standard_normal(int(np.prod(grid)))
+    z = host(P.apply(dev(r)))
+    s, zr = PB.apply_scale(f, r)
+    kf, amp = PB.sensitivity(grid, bands, f, r, s, schur="beta")
+    ex = P.export()
+    for k, ref in (("l2", f.Py), ("l1", f.To), ("minv", 1.0 / f.M)):
+        err = np.abs(host(ex[k]) - ref)
+        assert np.all(err <= PB.factor_tol(grid, kf) * np.abs(ref) + 1e-300), k
+    fg, _ = factors_of(P)
+    sg, zg = PB.apply_scale(fg, r)
+    assert PB.per_entry_ok(z, zg, sg, 1e-12)[0]
+    ok, worst = PB.per_entry_ok(z, zr, s, PB.e2e_tol(grid, amp))
+    assert ok, worst
+
+
+@pytest.mark.parametrize("grid", [(33, 5, 4), (350, 3, 4), (70, 24, 20)])
+def test_schur_beta_apply_parity_fp32(grid):
+    w = I.random_small(grid, 63, contrast_exp=3)
+    P = ffp.Preconditioner(grid, dev(w["kappa"]), w["bc"], "fp32", schur="beta")
+    bands = o.assemble(grid, w["kappa"], w["bc"])
+    r = np.random.default_rng(64).standard_normal(int(np.prod(grid)))
+    assert relerr(host(P.apply(dev(r))), o.apply(o.setup(grid, bands, schur="beta"), r)) <= 1e-5
+
+
+@pytest.mark.parametrize("precond", ["ntd", "combo"])
+def test_schur_beta_pcg_parity_fp64_blocks32(precond):
+    """PCG with X = beta on the 32^3 block workload (contrast 10^6): plain
+    B_NTD (standard PCG) and B_c (flexible CG) against the oracle: iterations
+    within one, solutions within 1e-7, both true residuals below 1e-8."""
+    wl = I.workload_blocks32(seed=0)
+    g, bc = wl["grid"], wl["bc"]
+    P = ffp.Preconditioner(g, dev(wl["kappa"]), bc, "fp64", precond=precond, schur="beta")
+    x, st = P.solve(dev(wl["b"]), rtol=1e-8, maxit=500)
+    bands = o.assemble(g, wl["kappa"], bc)
+    f = o.setup(g, bands, schur="beta")
+    ref = o.pcg(g, bands, f, wl["b"], rtol=1e-8, maxit=500, flexible=(precond == "combo"),
+                ilu=o.ilu0_setup(g, bands) if precond == "combo" else None)
+    assert st["status"] == 0 and ref["status"] == 0
+    assert abs(st["iters"] - ref["iters"]) <= 1
+    assert st["rel_res_true"] < 1e-8 and ref["relres"] < 1e-8
+    assert relerr(host(x), ref["x"]) <= 1e-7

@@ -95,3 +95,29 @@ def test_convnet_pins_catch_planted_mistake(name, tmp_path):
                         "-p", "no:cacheprovider"], cwd=work, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+# Mistakes planted in the oracle's X = beta form (FFP_SCHUR_BETA), caught by the
+# dense construction of tests/test_reading_study.py.
+SCHUR_BETA_MUTATIONS = {
+    "beta_form_level3_uses_newton": ("dk[e] -= C[e] * (c->classic ? beta[e] : xd) * C[e];",
+                                     "dk[e] -= C[e] * xd * C[e];"),
+    "beta_form_level3_keeps_offdiagonals": ("        if (c->classic) continue;                         /* X = beta: diagonal only */\n", ""),
+    "beta_form_level2_keeps_offdiagonal": ("if (a + 1 < nx && !c->classic) {", "if (a + 1 < nx) {"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SCHUR_BETA_MUTATIONS))
+def test_dense_construction_catches_planted_mistake(name, tmp_path):
+    old, new = SCHUR_BETA_MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "ffp_oracle.c")).read()
+    assert old in src, f"mutation anchor for {name} not found in the oracle"
+    work = tmp_path / "repo"
+    for sub in ("oracle", "tests", "paper_1909_09771_gb300"):
+        shutil.copytree(os.path.join(ROOT, sub), work / sub,
+                        ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*"))
+    (work / "oracle" / "ffp_oracle.c").write_text(src.replace(old, new))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_reading_study.py", "-q", "-x",
+                        "-p", "no:cacheprovider", "-k", "dense_construction"], cwd=work,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutation {name} survived:\n{r.stdout[-2000:]}"
