@@ -476,7 +476,7 @@ def run_batched(args):
         if not tuned:
             tuned.update(bat.tune())
         else:
-            bat.set_config(tuned["ilu_warps"], tuned["branches"])
+            bat.set_config(tuned["ilu_warps"], tuned["branches"], tuned["rhs_per_cta"])
         for x in xout:
             x.zero_()
         _, stats = bat.solve(rhs, xs=xout, rtol=RTOL, maxit=MAXIT, check=False)

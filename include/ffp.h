@@ -260,6 +260,10 @@ typedef struct {
                         under this configuration, as timed by ffp_batch_tune */
     double ntd_ms;   /* mean time (ms) of the B_NTD sweeps alone (3 launches per group) */
     int from_cache;  /* 1 if read from the tuning cache */
+    int rhs_per_cta; /* 1, or 2: two right-hand sides of an instance share one chain of apply
+                        CTAs (one stage of factor records, two pairs of compute warps); only in
+                        groups where every instance's right-hand sides pair up and the two-RHS
+                        kernels are built (FP32/BF16 factors, short lines), else 1 is used */
 } ffp_batch_config;
 
 /* Bytes of the one device workspace of a batch (0 for invalid arguments).
@@ -280,13 +284,14 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
                     const ffp_bc *bcs, const double *const *t, int nrhs, int precision,
                     int precond, void *workspace, size_t ws_bytes, void *stream, ffp_batch **out);
 
-/* Choose the launch configuration by timing the batched preconditioner on
- * this batch (it overwrites the pairs' internal vectors, none of the caller's).
- * cache_path: NULL, or a text file of "<key> <ilu_warps> <branches> <ms> <ntd_ms>"
- * lines; a line whose key (GPU, precision, preconditioner, grids, nrhs)
+/* Choose the launch configuration (ILU(0) warps per CTA, branches, right-hand
+ * sides per apply CTA) by timing the batched preconditioner on this batch (it
+ * overwrites the pairs' internal vectors, none of the caller's).
+ * cache_path: NULL, or a text file of "<key> <ilu_warps> <branches> <ms> <ntd_ms>
+ * <rhs_per_cta>" lines; a line whose key (GPU, precision, preconditioner, grids, nrhs)
  * matches is used without timing (ms and ntd_ms are then the cached ones),
  * else the choice is appended.  out may be NULL.  A batch that is never tuned
- * uses ilu_warps 4, branches 1. */
+ * uses ilu_warps 4, branches 1, rhs_per_cta 1. */
 int ffp_batch_tune(ffp_batch *B, const char *cache_path, ffp_batch_config *out, void *stream);
 int ffp_batch_get_config(const ffp_batch *B, ffp_batch_config *cfg);
 int ffp_batch_set_config(ffp_batch *B, const ffp_batch_config *cfg);

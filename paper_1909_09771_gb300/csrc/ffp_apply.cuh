@@ -82,10 +82,12 @@ struct ApplyView {
     R *z;          // output (holds y after the lower sweeps)
     R *scr;        // 2 planes of scratch (phase 2 intermediates)
     int *flags;    // error flags (FL_TIMEOUT)
-    __device__ __forceinline__ explicit ApplyView(const ApplyArgs &a)
+    // the view of right-hand side q (0, or 1 for the second of a two-RHS entry)
+    __device__ __forceinline__ ApplyView(const ApplyArgs &a, int q)
         : nx(a.nx), ny(a.ny), nz(a.nz), rec(static_cast<const F *>(a.rec)),
-          l3n(static_cast<const F *>(a.l3n)), r(static_cast<const R *>(a.r)),
-          z(static_cast<R *>(a.z)), scr(static_cast<R *>(a.scr)), flags(a.flags) {}
+          l3n(static_cast<const F *>(a.l3n)), r(static_cast<const R *>(q ? a.r1 : a.r)),
+          z(static_cast<R *>(q ? a.z1 : a.z)), scr(static_cast<R *>(q ? a.scr1 : a.scr)),
+          flags(q ? a.flags1 : a.flags) {}
 };
 
 constexpr int kSmemBudget = 220 * 1024;
@@ -142,9 +144,10 @@ __device__ __forceinline__ void st_slots(R *p, const R (&x)[S], int cnt) {
     }
 }
 
-// Compile-time stage layout for phase PH: fields [NF][32][SP] F, twist-cell
-// blocks [NM][8] F, vector row blocks [NV][32 SP + 32] R (SP = slot_pitch(S)).
-template <int S, typename F, int PH>
+// Compile-time stage layout for phase PH and NR right-hand sides: fields
+// [NF][32][SP] F (shared by the right-hand sides), twist-cell blocks [NM][8] F,
+// vector row blocks [NR][NV][32 SP + 32] R (SP = slot_pitch(S)).
+template <int S, typename F, int PH, int NR = 1>
 struct Stage {
     using R = typename Compute<F>::type;
     static constexpr int NF = 5;  // alpha, gamma, minv, l2, l3
@@ -156,10 +159,10 @@ struct Stage {
     static constexpr int kVecOff = ((NF * kFld + NM * kMid + 15) / 16) * 16;
     static constexpr int kVec = (32 * SP + 32) * (int)sizeof(R);
     // twist caches + full/empty mbarriers of both rings
-    static constexpr int kExtra = 2 * (S + 1) * 32 * (int)sizeof(R) + 2 * 2 * 5 * 8;
-    __host__ __device__ static constexpr int bytes_v(int vst) { return kVecOff + (vst ? NV * kVec : 0); }
+    static constexpr int kExtra = 2 * NR * (S + 1) * 32 * (int)sizeof(R) + 2 * 2 * 5 * 8;
+    __host__ __device__ static constexpr int bytes_v(int vst) { return kVecOff + (vst ? NR * NV * kVec : 0); }
     __host__ __device__ static constexpr int total(int nst, int vst, int nx) {
-        return 2 * nst * bytes_v(vst) + kExtra + 4 * nx * (int)sizeof(R);
+        return 2 * nst * bytes_v(vst) + kExtra + NR * 4 * nx * (int)sizeof(R);
     }
     // vector rows are staged if three stages of them fit beside the longest gbuf
     static constexpr int VST = total(3, 1, FFP_MAX_NX) <= kSmemBudget ? 1 : 0;
@@ -173,6 +176,14 @@ struct Stage {
     static constexpr int kBytes = bytes_v(VST);
 };
 
+// The two-RHS form is built where its stage ring keeps at least three stages
+// with staged rows in every phase.
+template <int S, typename F>
+__host__ __device__ constexpr bool two_rhs_fits() {
+    return Stage<S, F, 0, 2>::VST && Stage<S, F, 1, 2>::VST && Stage<S, F, 2, 2>::VST &&
+           Stage<S, F, 0, 2>::NST >= 3 && Stage<S, F, 1, 2>::NST >= 3 && Stage<S, F, 2, 2>::NST >= 3;
+}
+
 // One CTA per level-3 half (phases 0, 2) or per twist plane (phase 1) of one
 // pair: the pair is A0, or table[blockIdx.y] when a table is given; a pair
 // whose control word is given and has bit 0 clear returns at once.
@@ -184,22 +195,26 @@ struct Stage {
 constexpr int kProducers = 2;
 constexpr int kApplyThreads = 256;
 
-template <int S, typename F, int PH>
+template <int S, typename F, int PH, int NR>
 __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, const ApplyArgs *__restrict__ table) {
     using R = typename Compute<F>::type;
     const ApplyArgs &src = table ? table[blockIdx.y] : A0;
-    if (src.ctl && !(*src.ctl & 1)) return;  // a batched pair that does not iterate now
-    const ApplyView<F> A(src);
+    // a batched entry none of whose pairs iterates now
+    if (src.ctl && !(*src.ctl & 1) && (NR == 1 || (src.ctl1 && !(*src.ctl1 & 1)))) return;
     const unsigned wtries = src.wait_tries;
     const int stall = src.stall;
-    using SG = Stage<S, F, PH>;
+    const ApplyArgs &args = src;   // (the producer's record list below is also named src)
+    using SG = Stage<S, F, PH, NR>;
     constexpr int NF = SG::NF, NM = SG::NM, NV = SG::NV, NST = SG::NST, D = SG::D, VST = SG::VST;
     static_assert(SG::total(NST, VST, FFP_MAX_NX) <= kSmemBudget, "stage ring does not fit");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool idle = (warp == 4 || warp == 5);
-    const bool producer = warp >= 2 && !idle;
+    // warps 4 and 5 compute the second right-hand side (NR = 2), else only help initialise
+    const bool idle = (warp == 4 || warp == 5) && NR == 1;
+    const bool producer = (warp & 3) >= 2;
     const int wid = warp & 1;                  // the level-2 half this warp computes or feeds
+    const int q = (warp == 4 || warp == 5) ? 1 : 0;   // the right-hand side a compute warp serves
+    const ApplyView<F> A(src, producer ? 0 : q);
     const int ppar = (warp >= 6) ? 1 : 0;      // the steps this producer stages (g mod 2)
     const int nx = A.nx, ny = A.ny, nz = A.nz;
     const int nxy = nx * ny;
@@ -214,14 +229,14 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem_raw + 2 * (size_t)NST * SG::kBytes);
     unsigned long long *full = bars + wid * 2 * 5, *empty = full + 5;
     R *caches = reinterpret_cast<R *>(bars + 2 * 2 * 5);
-    R *tcache = caches + wid * (S + 1) * 32;
-    R *gbase = caches + 2 * (S + 1) * 32;
+    R *tcache = caches + (q * 2 + wid) * (S + 1) * 32;
+    R *gbase = caches + 2 * NR * (S + 1) * 32 + q * 4 * A.nx;
     if (threadIdx.x == 0) {
-        // bars[c*10 + q] = full[q], bars[c*10 + 5 + q] = empty[q] of compute warp c
+        // bars[c*10 + k] = full[k], bars[c*10 + 5 + k] = empty[k] of level-2 half c
         for (int c = 0; c < 2; ++c)
-            for (int q = 0; q < 5; ++q) {
-                mbar_init(bars + c * 10 + q, 32);     // full: one cp.async arrival per producer lane
-                mbar_init(bars + c * 10 + 5 + q, 1);  // empty: one arrival by the compute warp
+            for (int k = 0; k < 5; ++k) {
+                mbar_init(bars + c * 10 + k, 32);     // full: one cp.async arrival per producer lane
+                mbar_init(bars + c * 10 + 5 + k, NR); // empty: one arrival per compute warp of the half
             }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -259,6 +274,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
             if (use > 0 && !aborted && !mbar_wait(empty + slot, (use - 1) & 1, wtries)) {
                 aborted = true;
                 atomicOr(A.flags + FL_TIMEOUT, 1);
+                if (NR == 2) atomicOr(args.flags1 + FL_TIMEOUT, 1);
             }
             unsigned char *st = ring + slot * SG::kBytes;
             int i, other, cpl;
@@ -272,32 +288,34 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
             else if (kind == 1) { if (nl > 0) l2r = (long)i * ny + ((wid == 0) ? my - 1 : my); }
             else l2r = (long)i * ny + ((wid == 0) ? k : k - 1);
             const long bown = own * BL;
-            const R *v0 = nullptr, *v1 = nullptr, *v2 = nullptr;
+            // the step's vector rows: which vector (1 = r, 2 = z, 3 = scratch) at which block offset
+            int vk[3] = {0, 0, 0};
+            long vo[3] = {0, 0, 0};
             if (PH == 0) {
                 if (kind != 2) {
                     if (other >= 0) l3a = (long)cpl * ny + k;
-                    v0 = A.r + bown;
-                    if (kind == 0 && other >= 0 && 2 * t + 1 > D) v1 = A.z + ((long)other * ny + k) * BL;
+                    vk[0] = 1; vo[0] = bown;
+                    if (kind == 0 && other >= 0 && 2 * t + 1 > D) { vk[1] = 2; vo[1] = ((long)other * ny + k) * BL; }
                 } else if (2 * (nl - t) > D) {
-                    v0 = A.z + bown;
+                    vk[0] = 2; vo[0] = bown;
                 }
             } else if (PH == 1) {
                 if (kind != 2) {
-                    v0 = A.r + bown;
-                    if (mz > 0) { l3a = (long)(mz - 1) * ny + k; v1 = A.z + bown - (long)ny * BL; }
-                    if (mz < nz - 1) v2 = A.z + bown + (long)ny * BL;
+                    vk[0] = 1; vo[0] = bown;
+                    if (mz > 0) { l3a = (long)(mz - 1) * ny + k; vk[1] = 2; vo[1] = bown - (long)ny * BL; }
+                    if (mz < nz - 1) { vk[2] = 2; vo[2] = bown + (long)ny * BL; }
                 } else if (2 * (nl - t) > D) {
-                    v0 = A.z + bown;
+                    vk[0] = 2; vo[0] = bown;
                 }
             } else {
                 if (kind != 2) {
                     l3a = (long)cpl * ny + k;
                     // the first plane's neighbour is the twist plane, written by the previous launch
-                    if (fpl == 0 || (kind == 0 && 2 * t + 1 > D)) v0 = A.z + ((long)other * ny + k) * BL;
-                    if (kind == 1) v1 = A.z + bown;  // y of the twist line
+                    if (fpl == 0 || (kind == 0 && 2 * t + 1 > D)) { vk[0] = 2; vo[0] = ((long)other * ny + k) * BL; }
+                    if (kind == 1) { vk[1] = 2; vo[1] = bown; }  // y of the twist line
                 } else {
-                    if (2 * (nl - t) > D) v0 = A.scr + ((long)h * ny + k) * BL;
-                    v1 = A.z + bown;                 // y, written by phase 0/1
+                    if (2 * (nl - t) > D) { vk[0] = 3; vo[0] = ((long)h * ny + k) * BL; }
+                    vk[1] = 2; vo[1] = bown;                     // y, written by phase 0/1
                 }
             }
             // factor records: stage fields [0..2] own alpha, gamma, minv, [3] l2 field of
@@ -328,16 +346,20 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
                                    c * 16);
             }
             if (VST) {
-                const R *vs[3] = {v0, v1, v2};
                 constexpr int VC = SG::kVec / 16;  // 16-byte chunks of one row block
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    if (vs[v]) {
-                        unsigned char *dst = st + SG::kVecOff + v * SG::kVec;
-                        const unsigned char *src = reinterpret_cast<const unsigned char *>(vs[v]);
+                for (int qq = 0; qq < NR; ++qq) {
+                    const ApplyView<F> Aq(args, qq);
 #pragma unroll
-                        for (int c0 = 0; c0 < VC; c0 += 32)
-                            if (c0 + lane < VC) cp_async16(dst + (c0 + lane) * 16, src + (c0 + lane) * 16);
+                    for (int v = 0; v < NV; ++v) {
+                        if (vk[v]) {
+                            const R *base = (vk[v] == 1) ? Aq.r : ((vk[v] == 2) ? Aq.z : Aq.scr);
+                            unsigned char *dst = st + SG::kVecOff + (qq * NV + v) * SG::kVec;
+                            const unsigned char *sp = reinterpret_cast<const unsigned char *>(base + vo[v]);
+#pragma unroll
+                            for (int c0 = 0; c0 < VC; c0 += 32)
+                                if (c0 + lane < VC) cp_async16(dst + (c0 + lane) * 16, sp + (c0 + lane) * 16);
+                        }
                     }
                 }
             }
@@ -367,7 +389,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
         return to_r(reinterpret_cast<const F *>(st + NF * SG::kFld + j * SG::kMid)[w], R());
     };
     auto Vp = [&](const unsigned char *st, int v) -> const R * {
-        return reinterpret_cast<const R *>(st + SG::kVecOff + v * SG::kVec);
+        return reinterpret_cast<const R *>(st + SG::kVecOff + (q * NV + v) * SG::kVec);
     };
     // a row block (staged or in global memory): this lane's slots and the twist cell
     auto ldrow = [&](const R *blk, R (&o)[S], R &om) {
@@ -530,7 +552,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs A0, c
             if (lane == 0) gw[L.m] = (nl > 0) ? M_(st, 1, MID_L2) * wm : R(0);
             R b[S], bm;
             rhs(st, bk, pbase + (long)my * nx, A.z + oblk + (long)my * BL, false, true, pl, other, b, bm);
-            named_barrier(1, 64);
+            named_barrier(1 + q, 64);
 #pragma unroll
             for (int s = 0; s < S; ++s)
                 if (s < cnt) b[s] = b[s] - gbuf[cell[s]] - gbuf[nx + cell[s]];
@@ -615,17 +637,17 @@ inline cudaError_t step_profile_read(unsigned long long *host) {
 }
 #endif
 
-template <int S, typename F, int PH>
+template <int S, typename F, int PH, int NR = 1>
 static cudaError_t launch_phase(const ApplyArgs &a, const ApplyArgs *table, int nx_max, dim3 grid,
                                 cudaStream_t st) {
-    using SG = Stage<S, F, PH>;
+    using SG = Stage<S, F, PH, NR>;
     const size_t smem = (size_t)SG::total(SG::NST, SG::VST, nx_max);
-    cudaError_t e = cudaFuncSetAttribute(apply_kernel<S, F, PH>,
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel<S, F, PH, NR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(apply_kernel<S, F, PH>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(apply_kernel<S, F, PH, NR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    apply_kernel<S, F, PH><<<grid, kApplyThreads, smem, st>>>(a, table);
+    apply_kernel<S, F, PH, NR><<<grid, kApplyThreads, smem, st>>>(a, table);
     return cudaGetLastError();
 }
 
@@ -639,6 +661,7 @@ cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cuda
     a.scr = c.ws.ascr;
     a.flags = c.ws.flags;
     a.ctl = nullptr;
+    a.r1 = nullptr; a.z1 = nullptr; a.scr1 = nullptr; a.flags1 = nullptr; a.ctl1 = nullptr;
     a.wait_tries = c.dbg_tries ? c.dbg_tries : kWaitTries;
     a.stall = c.dbg_stall;
     a.r = c.ws.ra;
@@ -647,23 +670,36 @@ cudaError_t apply_for_slots(const KernelCtx &c, const double *r, double *z, cuda
     const int mz = (a.nz - 1) / 2;
     const bool halves = (mz > 0) || (a.nz - 1 - mz > 0);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
-    if (e == cudaSuccess && halves) e = launch_phase<S, F, 0>(a, nullptr, c.nx, dim3(2), st);
-    if (e == cudaSuccess) e = launch_phase<S, F, 1>(a, nullptr, c.nx, dim3(1), st);
-    if (e == cudaSuccess && halves) e = launch_phase<S, F, 2>(a, nullptr, c.nx, dim3(2), st);
+    if (e == cudaSuccess && halves) e = launch_phase<S, F, 0, 1>(a, nullptr, c.nx, dim3(2), st);
+    if (e == cudaSuccess) e = launch_phase<S, F, 1, 1>(a, nullptr, c.nx, dim3(1), st);
+    if (e == cudaSuccess && halves) e = launch_phase<S, F, 2, 1>(a, nullptr, c.nx, dim3(2), st);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess) e = launch_from_lb(c, c.ws.za, z, add, st);
     return e;
 }
 
-// All pairs of a device table at once (vectors already in the compute type).
-template <int S, typename F>
-cudaError_t apply_table_for_slots(const ApplyArgs *table, int npairs, int nx_max, cudaStream_t st) {
+// All entries of a device table at once (vectors already in the compute type);
+// nr = right-hand sides per entry (1, or 2 when the two-RHS form fits).
+template <int S, typename F, int NR>
+static cudaError_t apply_table_nr(const ApplyArgs *table, int n, int nx_max, cudaStream_t st) {
     ApplyArgs none;
     std::memset(&none, 0, sizeof(none));
-    cudaError_t e = launch_phase<S, F, 0>(none, table, nx_max, dim3(2, npairs), st);
-    if (e == cudaSuccess) e = launch_phase<S, F, 1>(none, table, nx_max, dim3(1, npairs), st);
-    if (e == cudaSuccess) e = launch_phase<S, F, 2>(none, table, nx_max, dim3(2, npairs), st);
+    cudaError_t e = launch_phase<S, F, 0, NR>(none, table, nx_max, dim3(2, n), st);
+    if (e == cudaSuccess) e = launch_phase<S, F, 1, NR>(none, table, nx_max, dim3(1, n), st);
+    if (e == cudaSuccess) e = launch_phase<S, F, 2, NR>(none, table, nx_max, dim3(2, n), st);
     return e;
+}
+
+template <int S, typename F>
+bool two_rhs_supported() { return two_rhs_fits<S, F>(); }
+
+template <int S, typename F>
+cudaError_t apply_table_for_slots(const ApplyArgs *table, int n, int nx_max, int nr, cudaStream_t st) {
+    if constexpr (two_rhs_fits<S, F>()) {
+        if (nr == 2) return apply_table_nr<S, F, 2>(table, n, nx_max, st);
+    }
+    if (nr != 1) return cudaErrorInvalidValue;
+    return apply_table_nr<S, F, 1>(table, n, nx_max, st);
 }
 
 }  // namespace ffp

@@ -4,7 +4,8 @@
 
 namespace ffp {
 #define FFP_INST(SS) template cudaError_t apply_for_slots<SS, __nv_bfloat16>(const KernelCtx &, const double *, double *, cudaStream_t, const cudaEvent_t *, const double *); \
-    template cudaError_t apply_table_for_slots<SS, __nv_bfloat16>(const ApplyArgs *, int, int, cudaStream_t);
+    template cudaError_t apply_table_for_slots<SS, __nv_bfloat16>(const ApplyArgs *, int, int, int, cudaStream_t); \
+    template bool two_rhs_supported<SS, __nv_bfloat16>();
 FFP_SLOT_LIST(FFP_INST)
 #undef FFP_INST
 }  // namespace ffp

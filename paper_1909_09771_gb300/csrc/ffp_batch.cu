@@ -226,6 +226,7 @@ constexpr int kSyncHead = 32;
 
 struct Group {
     int p0, np;  // device pair range
+    int q0, nq;  // the group's range in the two-RHS entry table; nq = 0: it has none
     int S, Si;   // apply and ILU(0) slot counts
     int nx_max, nb_max;
     int nitems;        // ILU(0) work items (planes) of the group's pairs
@@ -253,6 +254,7 @@ struct ffp_batch {
     int nb_max;
     PairArgs *dpairs;
     ApplyArgs *dapply;
+    ApplyArgs *dapply2;            // two-RHS entries (pairs (i, 2j) and (i, 2j + 1))
     IluArgs *dilu;
     SetupArgs *dsetup;
     IluPivArgs *dpiv;
@@ -285,6 +287,7 @@ size_t batch_layout(int count, const ffp_grid *grids, int nrhs, int prec, char *
     const int np = count * nrhs;
     char *t_pairs = take(sizeof(PairArgs) * np);
     char *t_apply = take(sizeof(ApplyArgs) * np);
+    char *t_apply2 = take(sizeof(ApplyArgs) * np);
     char *t_ilu = take(sizeof(IluArgs) * np);
     char *t_setup = take(sizeof(SetupArgs) * count);
     char *t_piv = take(sizeof(IluPivArgs) * count);
@@ -295,6 +298,7 @@ size_t batch_layout(int count, const ffp_grid *grids, int nrhs, int prec, char *
     char *t_scal = take(kPairScal * np);
     if (B) {
         B->dpairs = (PairArgs *)t_pairs; B->dapply = (ApplyArgs *)t_apply; B->dilu = (IluArgs *)t_ilu;
+        B->dapply2 = (ApplyArgs *)t_apply2;
         B->dsetup = (SetupArgs *)t_setup; B->dpiv = (IluPivArgs *)t_piv; B->dctl = (int *)t_ctl;
         B->dsync = (int *)t_sync;
         B->dscal = t_scal;
@@ -356,7 +360,9 @@ cudaError_t group_precond(const ffp_batch *B, const Group &g, cudaStream_t s) {
     if (e == cudaSuccess) {
         if (f32) b_prec_in<float><<<gv, kThreads, 0, s>>>(T, combo);
         else b_prec_in<double><<<gv, kThreads, 0, s>>>(T, combo);
-        e = launch_apply_table(B->prec, g.S, B->dapply + g.p0, g.np, g.nx_max, s);
+        e = (B->cfg.rhs_per_cta == 2 && g.nq > 0)
+                ? launch_apply_table(B->prec, g.S, B->dapply2 + g.q0, g.nq, g.nx_max, 2, s)
+                : launch_apply_table(B->prec, g.S, B->dapply + g.p0, g.np, g.nx_max, 1, s);
     }
     if (e == cudaSuccess) {
         if (f32) b_prec_out<float><<<gv, kThreads, 0, s>>>(T, combo);
@@ -478,17 +484,18 @@ std::string batch_key(const ffp_batch *B) {
     return buf;
 }
 
-// cache lines: "<key> <ilu_warps> <branches> <ms> <ntd_ms>"
+// cache lines: "<key> <ilu_warps> <branches> <ms> <ntd_ms> <rhs_per_cta>"
 bool cache_lookup(const char *path, const std::string &key, ffp_batch_config *cfg) {
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
     char k[512];
-    int w = 0, br = 0;
+    int w = 0, br = 0, nr = 0;
     double ms = 0.0, nms = 0.0;
     bool found = false;
-    while (std::fscanf(f, "%511s %d %d %lf %lf", k, &w, &br, &ms, &nms) == 5)
-        if (key == k && w >= 1 && w <= 8 && (br == 0 || br == 1)) {
+    while (std::fscanf(f, "%511s %d %d %lf %lf %d", k, &w, &br, &ms, &nms, &nr) == 6)
+        if (key == k && w >= 1 && w <= 8 && (br == 0 || br == 1) && (nr == 1 || nr == 2)) {
             cfg->ilu_warps = w; cfg->branches = br; cfg->ms = ms; cfg->ntd_ms = nms;
+            cfg->rhs_per_cta = nr;
             found = true;  // the last matching line wins
         }
     std::fclose(f);
@@ -498,7 +505,8 @@ bool cache_lookup(const char *path, const std::string &key, ffp_batch_config *cf
 void cache_store(const char *path, const std::string &key, const ffp_batch_config &cfg) {
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %.6f %.6f\n", key.c_str(), cfg.ilu_warps, cfg.branches, cfg.ms, cfg.ntd_ms);
+    std::fprintf(f, "%s %d %d %.6f %.6f %d\n", key.c_str(), cfg.ilu_warps, cfg.branches, cfg.ms, cfg.ntd_ms,
+                 cfg.rhs_per_cta);
     std::fclose(f);
 }
 
@@ -542,7 +550,7 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
     B->g_iter = nullptr; B->g_resid = nullptr;
     B->iter_launches = 0; B->resid_launches = 0; B->setup_launches = 0;
     B->cfg.ilu_warps = 4; B->cfg.branches = 1; B->cfg.ms = 0.0; B->cfg.ntd_ms = 0.0;
-    B->cfg.from_cache = 0;
+    B->cfg.from_cache = 0; B->cfg.rhs_per_cta = 1;
     B->inst.resize(count);
     B->pairs.assign(B->npairs, PairArgs());
     std::memset(B->pairs.data(), 0, sizeof(PairArgs) * B->npairs);
@@ -688,6 +696,7 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
         A.scr = ascr[up];
         A.flags = P.flags;
         A.ctl = P.ctl;
+        A.r1 = nullptr; A.z1 = nullptr; A.scr1 = nullptr; A.flags1 = nullptr; A.ctl1 = nullptr;
         A.wait_tries = kWaitTries;
         A.stall = 0;
         IluArgs &L = it[k];
@@ -706,6 +715,7 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
     B->pairs = pt;
     // groups; each gets its ILU(0) sync region: counters, then its pairs' ready flags
     int *sync = B->dsync;
+    std::vector<ApplyArgs> at2;
     for (int k0 = 0; k0 < B->npairs;) {
         Group g;
         g.p0 = k0;
@@ -728,6 +738,22 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
             ready += (size_t)P.ny * P.nz;
         }
         g.np = k1 - k0;
+        g.q0 = (int)at2.size();
+        g.nq = 0;
+        // two-RHS entries: consecutive pairs (i, 2j), (i, 2j + 1) of one instance, if every
+        // pair of the group has its partner and the two-RHS kernels exist for its slot count
+        bool pairs_up = (g.np % 2 == 0) && apply_two_rhs_ok(precision, g.S);
+        for (int k = k0; k < k1 && pairs_up; k += 2)
+            pairs_up = (ord[k] % 2 == 0) && (ord[k + 1] == ord[k] + 1) && (ord[k] / nrhs == ord[k + 1] / nrhs);
+        if (pairs_up) {
+            for (int k = k0; k < k1; k += 2) {
+                ApplyArgs E = at[k];
+                const ApplyArgs &P2 = at[k + 1];
+                E.r1 = P2.r; E.z1 = P2.z; E.scr1 = P2.scr; E.flags1 = P2.flags; E.ctl1 = P2.ctl;
+                at2.push_back(E);
+            }
+            g.nq = g.np / 2;
+        }
         g.sync_bytes = 4 * (size_t)(ready - sync);
         sync = ready;
         B->groups.push_back(g);
@@ -738,6 +764,8 @@ int ffp_batch_setup(int count, const ffp_grid *grids, const double *const *kappa
         e = cudaMemcpyAsync(B->dapply, at.data(), sizeof(ApplyArgs) * B->npairs, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->dilu, it.data(), sizeof(IluArgs) * B->npairs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !at2.empty())
+        e = cudaMemcpyAsync(B->dapply2, at2.data(), sizeof(ApplyArgs) * at2.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->dctl, 0, 4 * (size_t)B->npairs, st);
     // padding positions of the apply input blocks must read 0; b_prec_in writes only cells;
     // ILU(0) epochs start at 0 and the tagged words untagged
@@ -810,9 +838,12 @@ int ffp_batch_get_config(const ffp_batch *B, ffp_batch_config *cfg) {
 
 int ffp_batch_set_config(ffp_batch *B, const ffp_batch_config *cfg) {
     if (!B || !cfg) return FFP_ERR_ARG;
-    if (cfg->ilu_warps < 1 || cfg->ilu_warps > 8 || (cfg->branches != 0 && cfg->branches != 1))
+    if (cfg->ilu_warps < 1 || cfg->ilu_warps > 8 || (cfg->branches != 0 && cfg->branches != 1) ||
+        (cfg->rhs_per_cta != 1 && cfg->rhs_per_cta != 2))
         return FFP_ERR_ARG;
-    if (cfg->ilu_warps != B->cfg.ilu_warps || cfg->branches != B->cfg.branches) drop_graphs(B);
+    if (cfg->ilu_warps != B->cfg.ilu_warps || cfg->branches != B->cfg.branches ||
+        cfg->rhs_per_cta != B->cfg.rhs_per_cta)
+        drop_graphs(B);
     B->cfg = *cfg;
     return FFP_OK;
 }
@@ -845,14 +876,18 @@ int ffp_batch_tune(ffp_batch *B, const char *cache_path, ffp_batch_config *out, 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->dctl, B->hctl, 4 * (size_t)B->npairs, cudaMemcpyHostToDevice, B->gs);
     const bool combo = B->precond == FFP_PRECOND_COMBO;
+    bool any_two = false;
+    for (const Group &g : B->groups) any_two = any_two || g.nq > 0;
     std::vector<ffp_batch_config> cand;
-    for (int br = 0; br <= 1; ++br)
-        for (int w : {1, 2, 4, 8}) {
-            if (!combo && w != 4) continue;
-            ffp_batch_config c;
-            c.ilu_warps = w; c.branches = br; c.ms = 0.0; c.ntd_ms = 0.0; c.from_cache = 0;
-            cand.push_back(c);
-        }
+    for (int nr = 1; nr <= (any_two ? 2 : 1); ++nr)
+        for (int br = 0; br <= 1; ++br)
+            for (int w : {1, 2, 4, 8}) {
+                if (!combo && w != 4) continue;
+                ffp_batch_config c;
+                c.ilu_warps = w; c.branches = br; c.ms = 0.0; c.ntd_ms = 0.0; c.from_cache = 0;
+                c.rhs_per_cta = nr;
+                cand.push_back(c);
+            }
     // mean time of 3 replays (after one warm-up replay) of the graph of fn over all groups
     auto time_graph = [&](auto fn, double *ms_out) -> cudaError_t {
         cudaGraphExec_t g = nullptr;
@@ -874,13 +909,16 @@ int ffp_batch_tune(ffp_batch *B, const char *cache_path, ffp_batch_config *out, 
     };
     auto precond_fn = [&](const Group &gr, cudaStream_t s) { return group_precond(B, gr, s); };
     auto ntd_fn = [&](const Group &gr, cudaStream_t s) {
-        return launch_apply_table(B->prec, gr.S, B->dapply + gr.p0, gr.np, gr.nx_max, s);
+        return (B->cfg.rhs_per_cta == 2 && gr.nq > 0)
+                   ? launch_apply_table(B->prec, gr.S, B->dapply2 + gr.q0, gr.nq, gr.nx_max, 2, s)
+                   : launch_apply_table(B->prec, gr.S, B->dapply + gr.p0, gr.np, gr.nx_max, 1, s);
     };
     double best_ms = 1e300;
     const ffp_batch_config keep = B->cfg;
     for (size_t q = 0; q < cand.size() && e == cudaSuccess; ++q) {
         B->cfg.ilu_warps = cand[q].ilu_warps;
         B->cfg.branches = cand[q].branches;
+        B->cfg.rhs_per_cta = cand[q].rhs_per_cta;
         e = time_graph(precond_fn, &cand[q].ms);
         if (e == cudaSuccess && cand[q].ms < best_ms) {
             best_ms = cand[q].ms;
@@ -890,6 +928,7 @@ int ffp_batch_tune(ffp_batch *B, const char *cache_path, ffp_batch_config *out, 
     if (e == cudaSuccess) {
         B->cfg.ilu_warps = best.ilu_warps;
         B->cfg.branches = best.branches;
+        B->cfg.rhs_per_cta = best.rhs_per_cta;
         e = time_graph(ntd_fn, &best.ntd_ms);
     }
     B->cfg = keep;

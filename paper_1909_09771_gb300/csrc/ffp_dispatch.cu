@@ -12,7 +12,9 @@ template <int S, typename F>
 cudaError_t apply_for_slots(const KernelCtx &, const double *, double *, cudaStream_t,
                             const cudaEvent_t *, const double *);
 template <int S, typename F>
-cudaError_t apply_table_for_slots(const ApplyArgs *, int, int, cudaStream_t);
+cudaError_t apply_table_for_slots(const ApplyArgs *, int, int, int, cudaStream_t);
+template <int S, typename F>
+bool two_rhs_supported();
 
 cudaError_t launch_setup(const KernelCtx &c, const double *t, cudaStream_t st) {
     switch (c.slots) {
@@ -55,22 +57,41 @@ cudaError_t launch_apply(const KernelCtx &c, const double *r, double *z, cudaStr
 }
 
 template <typename F>
-static cudaError_t apply_table_t(int slots, const ApplyArgs *t, int n, int nxm, cudaStream_t st) {
+static cudaError_t apply_table_t(int slots, const ApplyArgs *t, int n, int nxm, int nr, cudaStream_t st) {
     switch (slots) {
-#define FFP_CASE(SS) case SS: return apply_table_for_slots<SS, F>(t, n, nxm, st);
+#define FFP_CASE(SS) case SS: return apply_table_for_slots<SS, F>(t, n, nxm, nr, st);
         FFP_SLOT_LIST(FFP_CASE)
 #undef FFP_CASE
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_apply_table(int prec, int slots, const ApplyArgs *table, int npairs, int nx_max,
+cudaError_t launch_apply_table(int prec, int slots, const ApplyArgs *table, int n, int nx_max, int nr,
                                cudaStream_t st) {
     switch (prec) {
-        case FFP_FP64: return apply_table_t<double>(slots, table, npairs, nx_max, st);
-        case FFP_FP32: return apply_table_t<float>(slots, table, npairs, nx_max, st);
-        case FFP_BF16: return apply_table_t<__nv_bfloat16>(slots, table, npairs, nx_max, st);
+        case FFP_FP64: return apply_table_t<double>(slots, table, n, nx_max, nr, st);
+        case FFP_FP32: return apply_table_t<float>(slots, table, n, nx_max, nr, st);
+        case FFP_BF16: return apply_table_t<__nv_bfloat16>(slots, table, n, nx_max, nr, st);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename F>
+static bool two_rhs_t(int slots) {
+    switch (slots) {
+#define FFP_CASE(SS) case SS: return two_rhs_supported<SS, F>();
+        FFP_SLOT_LIST(FFP_CASE)
+#undef FFP_CASE
+        default: return false;
+    }
+}
+
+bool apply_two_rhs_ok(int prec, int slots) {
+    switch (prec) {
+        case FFP_FP64: return two_rhs_t<double>(slots);
+        case FFP_FP32: return two_rhs_t<float>(slots);
+        case FFP_BF16: return two_rhs_t<__nv_bfloat16>(slots);
+        default: return false;
     }
 }
 

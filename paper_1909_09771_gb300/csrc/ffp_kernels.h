@@ -98,14 +98,24 @@ struct ApplyArgs {
     void *scr;        // 2 planes
     int *flags;
     const int *ctl;   // batched solves: the pair is skipped unless *ctl & 1 (null: always run)
+    // a second right-hand side of the same instance (the two-RHS form of the batched
+    // apply): its vectors, scratch, flags and control word (unused with one RHS)
+    const void *r1;
+    void *z1;
+    void *scr1;
+    int *flags1;
+    const int *ctl1;
     unsigned wait_tries;  // try limit of every mbarrier wait (kWaitTries; lowered by a test)
     int stall;        // test hook: 1 = the first producer of the first level-3 half withholds
                       // its first "stage full" signal in phase 0, so a compute warp's wait runs out
 };
 
-// ffp_dispatch.cu: NTD apply of every pair of a device table (one launch per phase)
-cudaError_t launch_apply_table(int prec, int slots, const ApplyArgs *table, int npairs, int nx_max,
+// ffp_dispatch.cu: NTD apply of every entry of a device table (one launch per phase); nr =
+// right-hand sides per entry (2: the entry's second pair in r1, z1, scr1, flags1, ctl1)
+cudaError_t launch_apply_table(int prec, int slots, const ApplyArgs *table, int n, int nx_max, int nr,
                                cudaStream_t st);
+// whether the two-RHS form of the apply is built for this precision and slot count
+bool apply_two_rhs_ok(int prec, int slots);
 
 // ffp_dispatch.cu: z = B_NTD^{-1} r (+ add, optional); ev (optional) = two events
 // recorded just before and just after the three sweep launches

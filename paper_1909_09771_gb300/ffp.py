@@ -58,7 +58,7 @@ class Stats(ctypes.Structure):
 
 class BatchConfig(ctypes.Structure):
     _fields_ = [("ilu_warps", ctypes.c_int), ("branches", ctypes.c_int), ("ms", ctypes.c_double),
-                ("ntd_ms", ctypes.c_double), ("from_cache", ctypes.c_int)]
+                ("ntd_ms", ctypes.c_double), ("from_cache", ctypes.c_int), ("rhs_per_cta", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -377,8 +377,8 @@ class Batch:
             raise FFPError(st, "ffp_batch_get_config")
         return c.as_dict()
 
-    def set_config(self, ilu_warps, branches):
-        c = BatchConfig(int(ilu_warps), int(branches), 0.0, 0.0, 0)
+    def set_config(self, ilu_warps, branches, rhs_per_cta=1):
+        c = BatchConfig(int(ilu_warps), int(branches), 0.0, 0.0, 0, int(rhs_per_cta))
         st = load().ffp_batch_set_config(self._h, ctypes.byref(c))
         if st != FFP_OK:
             raise FFPError(st, "ffp_batch_set_config")

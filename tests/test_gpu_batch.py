@@ -72,11 +72,15 @@ CASES = [("fp64", "combo", 3), ("fp32", "combo", 3), ("bf16", "combo", 3), ("fp6
          ("fp32", "ntd", 1)]
 
 
+@pytest.mark.parametrize("rhs_per_cta", [1, 2])
 @pytest.mark.parametrize("precision,precond,contrast", CASES)
-def test_pairs_equal_standalone_solves(precision, precond, contrast):
+def test_pairs_equal_standalone_solves(precision, precond, contrast, rhs_per_cta):
+    """rhs_per_cta = 2: the two right-hand sides of an instance share one chain of
+    apply CTAs (one factor stage ring, two pairs of compute warps)."""
     inst = instances(contrast)
     bat = make_batch(inst, precision, precond)
     assert bat.info()["groups"] == 4
+    bat.set_config(4, 1, rhs_per_cta)
     xs, stats = bat.solve(rhs_list(inst), rtol=1e-8, maxit=300, check=False)
     for i, (w, bs) in enumerate(inst):
         P = ffp.Preconditioner(w["grid"], dev(w["kappa"]), w["bc"], precision, precond=precond)
@@ -90,11 +94,13 @@ def test_pairs_equal_standalone_solves(precision, precond, contrast):
 
 
 def test_configuration_changes_no_result():
+    """ILU(0) warps, parallel or sequential groups and one or two right-hand
+    sides per apply CTA give bitwise identical solves."""
     inst = instances(3)
     bat = make_batch(inst, "fp32", "combo")
     out = []
-    for warps, branches in [(2, 0), (8, 1), (4, 1)]:
-        bat.set_config(warps, branches)
+    for warps, branches, nr in [(2, 0, 1), (8, 1, 2), (4, 1, 1), (2, 1, 2), (4, 0, 2)]:
+        bat.set_config(warps, branches, nr)
         xs, stats = bat.solve(rhs_list(inst), rtol=1e-8, maxit=300)
         out.append(([host(x) for x in xs], [s["iters"] for s in stats]))
     for xs, its in out[1:]:
@@ -113,7 +119,9 @@ def test_tune_and_cache(tmp_path):
     bat2 = make_batch(inst, "fp32", "combo")
     c2 = bat2.tune(cache)
     assert c2["from_cache"] == 1
-    assert (c2["ilu_warps"], c2["branches"]) == (c1["ilu_warps"], c1["branches"])
+    assert (c2["ilu_warps"], c2["branches"], c2["rhs_per_cta"]) == (c1["ilu_warps"], c1["branches"],
+                                                                     c1["rhs_per_cta"])
+    assert c1["rhs_per_cta"] in (1, 2)
     # the tuned batch still solves exactly as an untuned one
     xs, st = bat.solve(rhs_list(inst), rtol=1e-8, maxit=300)
     ref = make_batch(inst, "fp32", "combo")
