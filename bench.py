@@ -693,8 +693,8 @@ def run_reference(args):
 # DRAM bytes per launch from one ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum), by workload (and factor precision); absent = not measured for the
 # kernel as it now is.
-APPLY_TRAFFIC = {}
-SPMV_TRAFFIC = {}
+APPLY_TRAFFIC = {("grf350", "fp32"): 2676.0e6}   # the three sweep launches of one apply
+SPMV_TRAFFIC = {"grf350": 2657.7e6}
 
 
 def main():
