@@ -50,8 +50,13 @@ MAXIT = 1000
 # (l1, 1/M, l2, l3) in the storage precision + 4 FP64 vector passes (read r,
 # write y, read y, write z): 96 / 64 / 48 bytes for FP64 / FP32 / BF16 factors.
 NTD_BYTES = {"fp64": 2 * 4 * 8 + 4 * 8, "fp32": 2 * 4 * 4 + 4 * 8, "bf16": 2 * 4 * 2 + 4 * 8}
-# SpMV fused with (p, q): p 8 + q 8 + 4 FP64 bands 32 bytes per unknown.
+# SpMV fused with (p, q): p 8 + q 8 + 4 FP64 bands 32 bytes per unknown, and 8 FP64
+# operations on the FMA pipe per unknown (d x, six couplings, the (p, q) term).
 SPMV_BYTES = 48
+SPMV_FP64_OPS = 8
+# FP64 FMA-pipe operations per second of the part: 152 SMs x 2 FP64 FMA per clock x 2070 MHz
+# (the nominal 1.25 TFLOP/s FP64 at the maximum SM clock).
+FP64_OPS_PEAK = 152 * 2 * 2.07e9
 
 
 def make_workload(name, seed=0):
@@ -349,6 +354,7 @@ def run_ours(args):
     depth = (grid[2] + 1) * (grid[1] + 1)  # dependent line solves per apply
     spmv_per_ms = st["spmv_ms"] / max(st["iters"], 1)
     spmv_achieved = SPMV_BYTES * n / (spmv_per_ms * 1e-3) / 1e9 if spmv_per_ms > 0 else None
+    spmv_ops = SPMV_FP64_OPS * n / (spmv_per_ms * 1e-3) / 1e9 if spmv_per_ms > 0 else None
     reasons = sorted(set(clocks.get("reasons", [])) | set((fp64 or {}).get("clocks", {}).get("reasons", [])))
     clocks = dict(clocks, reasons=reasons)
     filt = ("rowsum" if net is None else
@@ -409,12 +415,16 @@ def run_ours(args):
         },
         "roofline_spmv": {
             "kernel": "spmv_dot_kernel (q = A p fused with (p, q))",
-            "bound": "hbm",
-            "achieved": spmv_achieved,
-            "peak": peak,
-            "unit": "GB/s",
-            "frac": (spmv_achieved / peak) if spmv_achieved else None,
-            "peak_kind": peak_kind,
+            "bound": "alu",
+            "achieved": spmv_ops,
+            "peak": FP64_OPS_PEAK / 1e9,
+            "unit": "G FP64 FMA-pipe ops/s",
+            "frac": (spmv_ops * 1e9 / FP64_OPS_PEAK) if spmv_ops else None,
+            "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clock x 2070 MHz (nominal 1.25 TFLOP/s FP64)",
+            "ops_per_unknown": SPMV_FP64_OPS,
+            "hbm_achieved_gbs": spmv_achieved,
+            "hbm_frac": (spmv_achieved / peak) if spmv_achieved else None,
+            "hbm_peak_kind": peak_kind,
             "traffic": SPMV_TRAFFIC.get(args.workload),
             "bytes_per_unknown": SPMV_BYTES,
             "ms_per_launch": spmv_per_ms,
