@@ -28,6 +28,23 @@
 
 namespace ffp {
 
+#ifdef FFP_STEP_PROFILE
+// Setup profile (profiling builds only): clock64 cycles of thread 0 of the first
+// level-3 half, accumulated over its planes: [0] level-2 factorization, of which
+// [5] line Schur terms, [6] line pivots, [7] line stores; [1] the w vector; [2] the
+// nested plane solve; [3] beta = v ./ w; [4] the Schur term of the next plane;
+// [8] planes; [9] the whole plane loop.
+static __device__ unsigned long long g_setup_prof[16];
+__device__ __forceinline__ unsigned long long setup_stamp() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%clock64;" : "=l"(t)::"memory");
+    return t;
+}
+#define FFP_SPROF(...) __VA_ARGS__
+#else
+#define FFP_SPROF(...)
+#endif
+
 // Store one factor entry in the storage precision.
 __device__ __forceinline__ void put_factor(void *base, long idx, double v, int prec) {
     if (prec == FFP_FP64) static_cast<double *>(base)[idx] = v;
@@ -293,7 +310,8 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
                              const double *Px, const double *Py, const double *tp, double *l1d,
                              double *mid, void *rec, void *l1n, long line0, int prec,
                              double *lbuf, double *meet, int wid, int lane, int cnt,
-                             int *flags, SlotSplit &sp, int classic) {
+                             int *flags, SlotSplit &sp, int classic,
+                             unsigned long long *prof = nullptr) {
     const int my = (ny - 1) / 2;
     const int nl = (wid == 0) ? my : ny - 1 - my;
     double *SB = lbuf + wid * 3 * nx, *SP = SB + nx, *SO = SP + nx;
@@ -313,6 +331,7 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
         }
         Tdm = Pd[o + L.m];
         Tom = Px[o + L.m];
+        FFP_SPROF(const unsigned long long q0 = setup_stamp();)
         if (t > 0) {
             const int kc = (wid == 0) ? k - 1 : k;
             line_schur<S>(L, nx, lane, cnt, st, Py + (long)kc * nx, tp ? tp + o : nullptr, SB, SP,
@@ -323,8 +342,12 @@ __device__ void level2_setup(const LineMap &L, int nx, int ny, const double *Pd,
             Tdm -= cdm;
             Tom -= com;
         }
+        FFP_SPROF(const unsigned long long q1 = setup_stamp();)
         factor_line<S>(L, lane, cnt, Td, To, Tdm, Tom, SO, st, flags, sp);
+        FFP_SPROF(const unsigned long long q2 = setup_stamp();)
         store_line<S>(L, lane, cnt, nx, k, st, l1d, mid, rec, l1n, line0, prec, sp);
+        FFP_SPROF(if (prof) { const unsigned long long q3 = setup_stamp();
+                              prof[5] += q1 - q0; prof[6] += q2 - q1; prof[7] += q3 - q2; })
     }
     // twist line: Schur terms from both halves
     {
@@ -387,7 +410,11 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
         const int nl3 = (h == 0) ? mz : nz - 1 - mz;
         double *l1d = A.ws.sF[h][0], *mid = A.ws.sF[h][1];
         double *W = A.ws.sW[h][0], *V = A.ws.sW[h][1];
+        FFP_SPROF(const bool sprof = h == 0 && blockIdx.y == 0 && tid == 0;
+                  unsigned long long pacc[16] = {0};
+                  const unsigned long long pstart = setup_stamp();)
         for (int t = 0; t < nl3; ++t) {
+            FFP_SPROF(const unsigned long long s0 = setup_stamp();)
             const int i = (h == 0) ? t : nz - 1 - t;
             const double *Pd, *Px, *Py;
             if (t == 0) {
@@ -402,24 +429,28 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
             if (wid < 4)
                 level2_setup<S>(L, nx, ny, Pd, Px, Py, A.t ? A.t + i * nxy : nullptr, l1d, mid,
                                 A.rec, A.l1n, (long)i * ny, A.prec, lbuf, meet, half, lane, cnt,
-                                flags, sp, A.schur);
+                                flags, sp, A.schur FFP_SPROF(, sprof ? pacc : nullptr));
+            FFP_SPROF(const unsigned long long s1 = setup_stamp();)
             const int dst = (t == nl3 - 1) ? mz : ((h == 0) ? i + 1 : i - 1);
             const int ic = (i < dst) ? i : dst;
             const double *C = A.cz + ic * nxy;
             for (long e = tid; e < nxy; e += blockDim.x)
                 W[e] = C[e] * (A.t ? A.t[dst * nxy + e] : 1.0);
             __syncthreads();
+            FFP_SPROF(const unsigned long long s2 = setup_stamp();)
             if (wid < 4) {
                 SetupPol pol{W, V, nx};
                 plane_solve<S, false, double, double>(L, nx, ny, l1d, mid, Py, pol, gbuf, half, lane,
                                                       cnt, sp);
             }
             __syncthreads();
+            FFP_SPROF(const unsigned long long s3 = setup_stamp();)
             for (long e = tid; e < nxy; e += blockDim.x) {
                 const bool z = fabs(W[e]) < 1e-300;  // one divide either way
                 V[e] = (z ? 1.0 : V[e]) / (z ? Pd[e] : W[e]);
             }
             __syncthreads();
+            FFP_SPROF(const unsigned long long s4 = setup_stamp();)
             const bool to_mid = (dst == mz);
             double *od = to_mid ? A.ws.sC[h][0] : A.ws.sP[h][(t + 1) & 1][0];
             double *ox = to_mid ? A.ws.sC[h][1] : A.ws.sP[h][(t + 1) & 1][1];
@@ -448,7 +479,14 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
                 }
             }
             __syncthreads();
+            FFP_SPROF(if (sprof) { const unsigned long long s5 = setup_stamp();
+                                   pacc[0] += s1 - s0; pacc[1] += s2 - s1; pacc[2] += s3 - s2;
+                                   pacc[3] += s4 - s3; pacc[4] += s5 - s4; pacc[8] += 1; })
         }
+        FFP_SPROF(if (sprof) {
+            pacc[9] = setup_stamp() - pstart;
+            for (int q = 0; q < 16; ++q) g_setup_prof[q] = pacc[q];
+        })
     } else {
         double *Pd = A.ws.sP[0][0][0], *Px = A.ws.sP[0][0][1], *Py = A.ws.sP[0][0][2];
         const long g0 = (long)mz * nxy;
@@ -478,6 +516,12 @@ __global__ void __launch_bounds__(256) setup_kernel(const __grid_constant__ Setu
     if (phase == 0 && A.nz <= 1) return;  // a single plane has no level-3 halves
     setup_body<S>(A, phase);
 }
+
+#ifdef FFP_STEP_PROFILE
+inline cudaError_t setup_profile_read(unsigned long long *host) {
+    return cudaMemcpyFromSymbol(host, g_setup_prof, sizeof(g_setup_prof));
+}
+#endif
 
 template <int S>
 cudaError_t setup_table_for_slots(const SetupArgs *table, int count, int nx_max, cudaStream_t st) {

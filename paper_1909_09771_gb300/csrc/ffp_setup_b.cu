@@ -9,3 +9,11 @@ namespace ffp {
 X(8) X(11)
 #undef X
 }  // namespace ffp
+
+#ifdef FFP_STEP_PROFILE
+// Profiling builds only (build.py --profile; not part of include/ffp.h): the setup
+// profile of the last setup with the slot counts of this unit, 16 counters.
+extern "C" int ffp_setup_profile(unsigned long long *host16) {
+    return ffp::setup_profile_read(host16) == cudaSuccess ? 0 : -2;
+}
+#endif

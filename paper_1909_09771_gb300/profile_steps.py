@@ -2,6 +2,12 @@
 build of the library (python -m paper_1909_09771_gb300.build --profile, which
 writes libffp_profile.so beside libffp.so; the normal library has no stamps).
 
+It also reports the setup's per-plane phases (slot counts 8 and 11, so
+nx from 130 to 353): the level-2 factorization of the plane (line Schur terms,
+line pivots, line stores), the w vector, the nested plane solve for beta-hat,
+beta = v ./ w, and the Schur term of the next plane, per plane of the first
+level-3 half.
+
 The profiling build stamps clock64 around the segments of every line step of
 one compute warp (level-2 half 0 of the first level-3 half, phase 0 launch)
 and reports, per lower- and upper-sweep step: the wait for its shared-memory
@@ -33,6 +39,14 @@ def budget(n, lib):
     if lib.ffp_step_profile(ctypes.cast(prof, ctypes.c_void_p)) != 0:
         raise RuntimeError("ffp_step_profile failed")
     p = list(prof)
+    sprof = (ctypes.c_ulonglong * 16)()
+    setup = None
+    if lib.ffp_setup_profile(ctypes.cast(sprof, ctypes.c_void_p)) == 0 and sprof[8] > 0:
+        q = list(sprof)
+        npl = q[8]
+        setup = {"planes": npl, "level2": q[0] / npl, "line_schur": q[5] / npl, "line_pivots": q[6] / npl,
+                 "line_store": q[7] / npl, "w": q[1] / npl, "plane_solve": q[2] / npl, "beta": q[3] / npl,
+                 "next_schur": q[4] / npl, "loop": q[9] / npl}
     depth = (w["grid"][2] + 1) * (w["grid"][1] + 1)
     ms = st["ntd_ms"] / max(st["napply"], 1)
     nl, nu = max(p[4], 1), max(p[9], 1)
@@ -45,6 +59,7 @@ def budget(n, lib):
                   "store_release": p[8] / nu, "total": sum(p[5:9]) / nu},
         "loop_cycles_per_step": p[10] / max(p[4] + p[9], 1),
         "first_try_misses": p[11],
+        "setup": setup,
     }
 
 
@@ -54,6 +69,8 @@ def main(argv):
     lib = ffp.load()
     lib.ffp_step_profile.argtypes = [ctypes.c_void_p]
     lib.ffp_step_profile.restype = ctypes.c_int
+    lib.ffp_setup_profile.argtypes = [ctypes.c_void_p]
+    lib.ffp_setup_profile.restype = ctypes.c_int
     for n in ([int(a) for a in argv] or [350]):
         r = budget(n, lib)
         print(f"grf{n} {r['grid']}: {r['ms_per_apply']:.2f} ms per apply, "
@@ -64,6 +81,12 @@ def main(argv):
                   f"{q['solve']:.0f}  store+release {q['store_release']:.0f}  total {q['total']:.0f} cycles")
         print(f"  plane loop {r['loop_cycles_per_step']:.0f} cycles per step; stage waits whose first "
               f"try failed: {r['first_try_misses']}")
+        q = r["setup"]
+        if q:
+            print(f"  setup, cycles per plane ({q['planes']} planes of one level-3 half): level-2 "
+                  f"{q['level2']:.0f} (line Schur {q['line_schur']:.0f}, pivots {q['line_pivots']:.0f}, "
+                  f"stores {q['line_store']:.0f}), w {q['w']:.0f}, plane solve {q['plane_solve']:.0f}, "
+                  f"beta {q['beta']:.0f}, next Schur {q['next_schur']:.0f}, loop {q['loop']:.0f}")
 
 
 if __name__ == "__main__":
