@@ -340,7 +340,7 @@ def run_ours(args):
         ms64, setup64, stats64, clocks64 = timed_steps(step64, kappa, b, x, args.fp64_steps, local)
         s64 = stats64[-1]
         fp64 = {"s": ms64 / 1e3, "setup_s": setup64 / 1e3, "iters": s64["iters"],
-                "rel_res_true": s64["rel_res_true"],
+                "rel_res_true": s64["rel_res_true"], "cond_est": s64["cond_est"],
                 "converged": all(s["status"] == 0 and s["rel_res_true"] < args.rtol for s in stats64),
                 "steps": args.fp64_steps, "warmup": "one setup + one apply (loads the FP64 kernels)",
                 "ms_per_apply_ntd": s64["ntd_ms"] / max(s64["napply"], 1),
@@ -387,6 +387,7 @@ def run_ours(args):
             "iters": st["iters"],
             "iters_rec": st["iters_rec"],
             "rel_res_true": st["rel_res_true"],
+            "cond_est": st["cond_est"],
             "converged": ok,
             "fp64_rowsum": fp64,
             "speedup_vs_fp64_rowsum": (fp64["s"] / (ms / 1e3)) if fp64 else None,

@@ -99,6 +99,13 @@ typedef struct {
                              checked then, was not yet below rtol and the solve went on */
     double spmv_ms;       /* device time of the iterations' q = A p launches (fused with
                              (p, q)), CUDA events on `stream`; 0 in batched solves */
+    double lanczos_min;   /* extreme eigenvalues of the Lanczos tridiagonal of B^{-1} A that the
+                             CG coefficients define (diagonal 1/alpha_k + beta_k/alpha_{k-1},
+                             off-diagonal sqrt(beta_k)/alpha_{k-1}, beta_k the coefficient that */
+    double lanczos_max;   /* formed p_k), over the iterations before the first restart; their
+                             ratio estimates cond(B^{-1} A).  With flexible CG it is an estimate
+                             of the same quantity.  0 when fewer than one iteration ran or in
+                             batched solves */
 } ffp_stats;
 
 typedef struct ffp_handle ffp_handle;

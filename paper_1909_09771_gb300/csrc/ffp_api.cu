@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "ffp_kernels.h"
 
@@ -111,6 +112,52 @@ long long ntd_launches(const KernelCtx &c) {
     return ((mz > 0 || c.nz - 1 - mz > 0) ? 3 : 1) + 2;
 }
 long long ilu_launches(const KernelCtx &c) { return ilu_solve_launches(c); }
+
+// Extreme eigenvalues of the Lanczos tridiagonal that k CG steps define (the
+// Lanczos-CG relation: with p_j = z_j + b_j p_{j-1}, b_0 = 0, the tridiagonal of
+// B^{-1}A in the basis of the preconditioned residuals has diagonal
+// 1/a_j + b_j/a_{j-1} and off-diagonal sqrt(b_j)/a_{j-1}).  Bisection on the
+// Sturm count (the number of negative pivots of T - s I), from the Gershgorin
+// interval, to the last bit.
+void lanczos_extremes(const std::vector<double> &a, const std::vector<double> &b, double *lmin,
+                      double *lmax) {
+    const size_t k = a.size();
+    *lmin = *lmax = 0.0;
+    if (k == 0) return;
+    std::vector<double> d(k), e2(k, 0.0);
+    double lo = 0.0, hi = 0.0;
+    for (size_t j = 0; j < k; ++j) {
+        if (!(a[j] > 0.0) || !(j == 0 || b[j] >= 0.0)) return;  // not a Lanczos sequence
+        d[j] = 1.0 / a[j] + (j > 0 ? b[j] / a[j - 1] : 0.0);
+        if (j > 0) e2[j] = b[j] / (a[j - 1] * a[j - 1]);
+    }
+    for (size_t j = 0; j < k; ++j) {
+        const double r = (j > 0 ? std::sqrt(e2[j]) : 0.0) + (j + 1 < k ? std::sqrt(e2[j + 1]) : 0.0);
+        if (j == 0 || d[j] - r < lo) lo = d[j] - r;
+        if (j == 0 || d[j] + r > hi) hi = d[j] + r;
+    }
+    auto below = [&](double s) {  // eigenvalues < s
+        int cnt = 0;
+        double q = 1.0;
+        for (size_t j = 0; j < k; ++j) {
+            q = d[j] - s - (j > 0 ? e2[j] / q : 0.0);
+            if (q == 0.0) q = -1e-300;
+            if (q < 0.0) ++cnt;
+        }
+        return cnt;
+    };
+    auto kth = [&](int want) {  // the eigenvalue with `want` eigenvalues below it
+        double l = lo, h = hi;
+        for (int it = 0; it < 200 && h - l > 0.0; ++it) {
+            const double m = 0.5 * (l + h);
+            if (m <= l || m >= h) break;
+            if (below(m) > want) h = m; else l = m;
+        }
+        return 0.5 * (l + h);
+    };
+    *lmin = kth(0);
+    *lmax = kth((int)k - 1);
+}
 
 // z = B^{-1} r for the handle's preconditioner (r and z distinct from c1, c2).
 // ev (optional): events recorded at the start, just before and just after the
@@ -264,6 +311,9 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
     double bb = 0.0, rr = 0.0;
     double pre_ms = 0.0, ntd_ms = 0.0, spmv_ms = 0.0;
     long long nl = 0;
+    // CG coefficients since the start, up to the first restart (Lanczos estimate)
+    std::vector<double> lz_a, lz_b;
+    bool lz_open = true;
 #define FFP_TRY(expr)                                                 \
     do {                                                              \
         cudaError_t _e = (expr);                                      \
@@ -299,6 +349,7 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
             if (best_true < 0.0 || rr < best_true) best_true = rr;
             if (stalls >= kStallConfirms) { status = FFP_ERR_NOT_CONVERGED; break; }
             fresh = 1;
+            lz_open = false;
         }
         if (it >= maxit) { status = FFP_ERR_NOT_CONVERGED; break; }
         FFP_TRY(precond_apply(c, c.ws.r, c.ws.z, st, &nl, h->ev));
@@ -315,6 +366,10 @@ int ffp_pcg_solve(ffp_handle *h, const double *b, double *x, double rtol, int ma
         nl += 8;
         ++it;
         if ((status = read_scalars(h, st)) != FFP_OK) goto done;
+        if (lz_open) {
+            lz_a.push_back(h->host_scal[SC_ALPHA]);
+            lz_b.push_back(lz_a.size() == 1 ? 0.0 : h->host_scal[SC_BETA]);
+        }
         {
             float a = 0.f, b2 = 0.f;
             if (cudaEventElapsedTime(&a, h->ev[0], h->ev[3]) == cudaSuccess) pre_ms += a;
@@ -347,6 +402,7 @@ done:
         }
         stats->launches = nl;
         stats->iters_rec = it_rec;
+        lanczos_extremes(lz_a, lz_b, &stats->lanczos_min, &stats->lanczos_max);
         stats->solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return status;

@@ -50,10 +50,13 @@ class Stats(ctypes.Structure):
                 ("rel_res_true", ctypes.c_double), ("solve_s", ctypes.c_double),
                 ("precond_ms", ctypes.c_double), ("ntd_ms", ctypes.c_double),
                 ("napply", ctypes.c_int), ("launches", ctypes.c_longlong), ("iters_rec", ctypes.c_int),
-                ("spmv_ms", ctypes.c_double)]
+                ("spmv_ms", ctypes.c_double), ("lanczos_min", ctypes.c_double),
+                ("lanczos_max", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["cond_est"] = (self.lanczos_max / self.lanczos_min) if self.lanczos_min > 0 else float("nan")
+        return d
 
 
 class BatchConfig(ctypes.Structure):

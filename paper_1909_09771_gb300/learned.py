@@ -222,6 +222,9 @@ def _main(argv=None):
     ev.add_argument("--exponent", type=float, default=2.0)
     ev.add_argument("--seeds", default="0,1")
     ev.add_argument("--precision", default="fp32")
+    ev.add_argument("--precond", default="combo,ntd",
+                    help="preconditioners to compare the filters with (combo = B_c, ntd = B_NTD)")
+    ev.add_argument("--maxit", type=int, default=1000)
     ev.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     ffp.load()
@@ -258,14 +261,19 @@ def _main(argv=None):
             t = predict_filter(net, w)
             torch.cuda.synchronize()
             row["infer_s"] = time.time() - t0
-            for name, tt in (("rowsum", None), ("learned", t)):
-                t0 = time.time()
-                P = ffp.Preconditioner(w["grid"], kap, w["bc"], a.precision, t=tt, precond="combo")
-                x, st = P.solve(b, rtol=1e-8, maxit=1000, check=False)
-                torch.cuda.synchronize()
-                row[name] = {"iters": st["iters"], "status": st["status"],
-                             "rel_res_true": st["rel_res_true"], "s": time.time() - t0}
-                P.close()
+            for pc in a.precond.split(","):
+                for name, tt in (("rowsum", None), ("learned", t)):
+                    t0 = time.time()
+                    P = ffp.Preconditioner(w["grid"], kap, w["bc"], a.precision, t=tt, precond=pc)
+                    x, st = P.solve(b, rtol=1e-8, maxit=a.maxit, check=False)
+                    torch.cuda.synchronize()
+                    # cond_est: Lanczos estimate of cond(B^{-1} A) from the CG coefficients
+                    row[f"{pc}_{name}"] = {"iters": st["iters"], "status": st["status"],
+                                           "rel_res_true": st["rel_res_true"],
+                                           "lanczos_min": st["lanczos_min"],
+                                           "lanczos_max": st["lanczos_max"],
+                                           "cond_est": st["cond_est"], "s": time.time() - t0}
+                    P.close()
             res.append(row)
             print(json.dumps(row), flush=True)
         if a.out:

@@ -290,6 +290,25 @@ def test_pcg_parity_fp64_grf32():
     # independent true residual with the oracle's operator
     xr = host(x)
     assert np.linalg.norm(w["b"] - o.spmv(g, bands, xr)) / np.linalg.norm(w["b"]) < 1e-8
+    # Lanczos estimate of cond(B^{-1} A) from the CG coefficients (O5): the same
+    # coefficients up to rounding, so the same extremes; the GPU's bisection
+    # against the oracle's dense eigensolver of its own tridiagonal
+    lmin, lmax = o.lanczos_extremes(ref["alpha"], ref["beta"])
+    assert abs(st["lanczos_min"] - lmin) <= 1e-6 * lmin
+    assert abs(st["lanczos_max"] - lmax) <= 1e-6 * lmax
+    assert st["cond_est"] == pytest.approx(lmax / lmin, rel=2e-6)
+
+
+def test_lanczos_estimate_of_a_known_spectrum():
+    """On a 1-D problem B = A exactly (level 1 is exact), so B^{-1} A = I: one
+    CG step, and the Lanczos tridiagonal is the 1 x 1 matrix [1]."""
+    grid = (40, 1, 1)
+    w = I.random_small(grid, 5, contrast_exp=3)
+    P = ffp.Preconditioner(grid, dev(w["kappa"]), w["bc"], "fp64")
+    _, st = P.solve(dev(w["b"]), rtol=1e-12, maxit=10)
+    assert st["iters"] == 1 and st["status"] == 0
+    assert st["lanczos_min"] == pytest.approx(1.0, rel=1e-12)
+    assert st["lanczos_max"] == pytest.approx(1.0, rel=1e-12)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
