@@ -339,12 +339,18 @@ void ffp_batch_destroy(ffp_batch *B);
  * channels 1 -> 16 -> 16 -> 16 -> 1, ReLU after the first three; output s,
  * t = exp(s).  Parameters: FP32 [FFP_NET_PARAMS], per layer the weights
  * w[out][in][dz][dy][dx] then the biases (offsets 0, 432 | 448, 7360 |
- * 7376, 14288 | 14304, 14736).  The convolutions use BF16 copies of the
- * weights (`wbf16`, the BF16 bit patterns, kept in step by ffp_net_cast or
- * ffp_net_adam) and FP32 arithmetic.  Batches hold `batch` instances of one
- * grid, instance-major: kappa [batch][N].
+ * 7376, 14288 | 14304, 14736).  The convolutions run on the tensor cores:
+ * BF16 copies of the weights (`wbf16`, the BF16 bit patterns, kept in step by
+ * ffp_net_cast or ffp_net_adam), BF16 features, activations and back-
+ * propagated gradients between layers, FP32 accumulation; s and the loss are
+ * FP32, the weight-gradient partial sums are folded in FP64.  Batches hold
+ * `batch` instances of one grid, instance-major: kappa [batch][N]; nx is at
+ * most FFP_NET_MAX_NX (a staged row of the padded grid must fit in shared
+ * memory).  Every call returns FFP_ERR_TIMEOUT if one of the kernels' bounded
+ * waits ran out.
  * ------------------------------------------------------------------------ */
 #define FFP_NET_PARAMS 14737
+#define FFP_NET_MAX_NX 1000
 
 /* Workspace bytes for a forward pass (train = 0) or a gradient (train = 1);
  * 0 for a bad grid or batch. */
@@ -357,15 +363,16 @@ int ffp_net_init(unsigned long long seed, float *params, unsigned short *wbf16, 
 /* wbf16 = BF16(params) (round to nearest even). */
 int ffp_net_cast(const float *params, unsigned short *wbf16, void *stream);
 
-/* t = exp(clamp(s, -30, 30)) [batch][N] FP64 device, s the network's output. */
+/* t = exp(clamp(s, -30, 30)) [batch][N] FP64 device, s the network's output.
+ * Synchronises `stream` (it reads the kernels' timeout flag). */
 int ffp_net_forward(const ffp_grid *grid, int batch, const double *kappa, const float *params,
                     const unsigned short *wbf16, void *workspace, size_t ws_bytes, double *t,
                     void *stream);
 
 /* Gradient of L = mean over cells of (s - s_target)^2 w.r.t. every parameter
  * (through the BF16 weights the forward pass used), into grad FP32
- * [FFP_NET_PARAMS] (device); loss: host pointer or NULL (then the call does
- * not synchronise).  s_target: FP32 [batch][N] device. */
+ * [FFP_NET_PARAMS] (device); loss: host pointer or NULL.  Synchronises
+ * `stream`.  s_target: FP32 [batch][N] device. */
 int ffp_net_grad(const ffp_grid *grid, int batch, const double *kappa, const float *s_target,
                  const float *params, const unsigned short *wbf16, void *workspace,
                  size_t ws_bytes, float *grad, double *loss, void *stream);

@@ -69,6 +69,7 @@ class BatchConfig(ctypes.Structure):
 
 FFP_BATCH_MAX_PAIRS = 65535
 FFP_NET_PARAMS = 14737
+FFP_NET_MAX_NX = 1000
 
 
 class FFPError(RuntimeError):

@@ -201,6 +201,64 @@ def predict_filter(net, w, device="cuda"):
     return net.forward(w["grid"], kap, batch=1)
 
 
+# Floating-point operations of the network per cell: useful ones (the 3x3x3
+# convolutions of 1 -> 16 -> 16 -> 16 -> 1 channels) and the ones the tensor
+# cores issue (every layer as 16 x 16 channels, the weight gradient with its
+# 128-row M of which 16 rows are used, plus the bias-gradient MMA), per cell
+# of the padded grid.
+USEFUL_FWD = 2 * 27 * (1 * 16 + 16 * 16 + 16 * 16 + 16 * 1)
+USEFUL_BWD = 2 * 27 * (1 * 16 + 16 * 16 + 16 * 16) + USEFUL_FWD  # data gradients of layers 3-1, weight gradients
+ISSUED_FWD = 4 * 27 * 2 * 16 * 16
+ISSUED_BWD = 3 * 27 * 2 * 16 * 16 + 4 * 28 * 2 * 128 * 16
+
+
+def bench(n=256, train_n=64, train_batch=8, reps=10):
+    """CUDA-event times of one forward pass at n^3 and one gradient (forward,
+    loss, backward) of a batch of train_n^3 instances, with the useful and
+    issued tensor-core TFLOP/s they reach."""
+    import json as _json
+    import os
+    dev = torch.device("cuda")
+    net = FilterNet(seed=0)
+    out = {}
+    peak = None
+    pk = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peak = _json.load(fh).get("bf16_tflops")
+    for label, grid, batch in (("forward", (n, n, n), 1), ("gradient", (train_n,) * 3, train_batch)):
+        cells = int(np.prod(grid)) * batch
+        padded = int(np.prod([v + 2 for v in grid])) * batch
+        kap = torch.as_tensor(np.concatenate([I.workload_grf(seed=k, n=grid[0], exponent=2.0)["kappa"]
+                                              for k in range(batch)]), device=dev)
+        if label == "forward":
+            t = torch.empty(cells, dtype=torch.float64, device=dev)
+            run = lambda: net.forward(grid, kap, batch=batch, t=t)
+            useful, issued = USEFUL_FWD * cells, ISSUED_FWD * padded
+        else:
+            st = torch.zeros(cells, dtype=torch.float32, device=dev)
+            gbuf = torch.empty(ffp.FFP_NET_PARAMS, dtype=torch.float32, device=dev)
+            run = lambda: net.grad(grid, kap, st, batch=batch, grad=gbuf, want_loss=False)
+            useful, issued = (USEFUL_FWD + USEFUL_BWD) * cells, (ISSUED_FWD + ISSUED_BWD) * padded
+        for _ in range(3):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[label] = {"grid": list(grid), "batch": batch, "ms": ms, "cells_per_s": cells / ms * 1e3,
+                      "useful_tflops": useful / ms / 1e9, "issued_tflops": issued / ms / 1e9,
+                      "issued_frac_of_bf16_peak": (issued / ms / 1e9 / peak) if peak else None}
+    out["peak_bf16_tflops"] = peak
+    out["note"] = ("whole calls: guard zeroing, weight images, features, the four convolutions (and "
+                   "the backward pass), the head, and the call's final synchronisation")
+    return out
+
+
 def _main(argv=None):
     import argparse
     import json
@@ -226,9 +284,17 @@ def _main(argv=None):
                     help="preconditioners to compare the filters with (combo = B_c, ntd = B_NTD)")
     ev.add_argument("--maxit", type=int, default=1000)
     ev.add_argument("--out", default=None)
+    bn = sub.add_parser("bench", help="time the network's forward pass and gradient (CUDA events)")
+    bn.add_argument("--n", type=int, default=256, help="forward pass on one n^3 instance")
+    bn.add_argument("--train-n", type=int, default=64)
+    bn.add_argument("--train-batch", type=int, default=8)
+    bn.add_argument("--reps", type=int, default=10)
     a = ap.parse_args(argv)
     ffp.load()
     dev = torch.device("cuda")
+    if a.cmd == "bench":
+        print(json.dumps(bench(a.n, a.train_n, a.train_batch, a.reps)))
+        return
     if a.cmd == "train":
         t0 = time.time()
         insts = I.workload_learned_train(count=a.count, n=a.n)

@@ -46,6 +46,21 @@ def test_workspace_bytes_host_only(lib):
     assert lib.ffp_workspace_bytes(ctypes.byref(g), 7) == 0
 
 
+def test_net_workspace_bytes_host_only(lib):
+    """The network's padded BF16 layout: two 16-byte planes per padded cell and
+    batch, with guards; rows longer than FFP_NET_MAX_NX cells are rejected."""
+    f = lib.ffp_net_workspace_bytes
+    f.restype = ctypes.c_size_t
+    g = ffp.Grid(64, 64, 64, 1, 1, 1)
+    inf, trn = f(ctypes.byref(g), 1, 0), f(ctypes.byref(g), 1, 1)
+    padded = 66 ** 3 * 32
+    assert 2 * padded <= inf < 3 * padded and 7 * padded <= trn < 8 * padded + (64 << 20)
+    g = ffp.Grid(ffp.FFP_NET_MAX_NX + 1, 2, 2, 1, 1, 1)
+    assert f(ctypes.byref(g), 1, 0) == 0
+    g = ffp.Grid(4, 4, 4, 1, 1, 1)
+    assert f(ctypes.byref(g), 0, 0) == 0
+
+
 def test_strerror_and_null_args(lib):
     assert lib.ffp_strerror(0) == b"ok"
     assert b"breakdown" in lib.ffp_strerror(ffp.FFP_ERR_BREAKDOWN)

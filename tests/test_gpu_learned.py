@@ -1,12 +1,30 @@
 """Learned filter on the GPU (include/ffp.h, "Learned filter") against the FP64
 oracle of oracle/convnet.py.
 
-Tolerances: the GPU network computes in FP32 with BF16 weights; the oracle runs
-in FP64 on the same BF16-rounded weights and FP32 biases, so the only
-difference is FP32 rounding: about 1e-7 per operation over 432-term sums and,
-for the weight gradient, sums over every cell of a batch.
-  forward s            1e-5 of max |s|
-  gradient, per layer  1e-4 relative 2-norm (reductions over ~10^4-10^5 cells)
+The GPU network runs its convolutions on the tensor cores: BF16 weights, BF16
+features, activations and back-propagated gradients between layers, FP32
+accumulation.  Two references:
+  * the oracle's conv3d / conv3d_backward composed with BF16 rounding at the
+    points where the GPU stores BF16 (`ref_forward_bf16`, `ref_backward_bf16`).
+    Then the only differences are FP32 against FP64 accumulation (about 1e-7
+    relative over 432-term sums) and the rare BF16 rounding decisions those
+    flip (one activation moves by one BF16 ulp, 2^-8 relative):
+      forward s           max error 2e-3 of max |s|, relative 2-norm 1e-3
+      gradient, per layer relative 2-norm 2e-3
+      loss                1e-4 relative
+  * the plain FP64 oracle (no rounding): the network's BF16 error itself.  For
+    s it is held to 1e-2 relative (2-norm).  A weight gradient is a sum over
+    cells of gz * x with heavy cancellation (its norm can be 1e-2 of the sum of
+    the terms' magnitudes), so its error is measured against that sum:
+    ||g - g64|| <= 2e-2 ||sum_q |gz_q| |x_q+off|||.  Every term carries at most
+    four BF16 storage roundings of 2^-9 (the stored input or activation, the
+    loss gradient, up to two back-propagated gradients), 8e-3 in all, and the
+    ReLU masks of cells whose pre-activation lies within a rounding of zero can
+    flip; measured on the oracle, the ratio stays below 6e-3 on grids of
+    10^3 cells and more.  On a grid of a few tens of cells one flipped mask is
+    a sizeable part of every sum, so this bar applies from 1000 cells on; the
+    BF16-storage reference holds the kernels on every grid.
+Other tolerances:
   Adam step            1e-6 relative (a few FP32 operations per parameter)
   Lanczos (FP64)       Ritz values 1e-8 relative; Ritz vectors A-cosine >= 1 - 1e-6
                        (same algorithm; the GPU's factors differ from the oracle's
@@ -74,23 +92,59 @@ def net_with_biases(seed):
     return net
 
 
-# several tiles (32 x 4 x 2) with ragged edges in every direction, and a tiny grid
+def ref_forward_bf16(par, x0):
+    """The oracle's layers with the GPU's BF16 storage: features and the three
+    hidden activations rounded to BF16, FP64 arithmetic otherwise."""
+    h = C.bf16_round(x0)
+    acts = [h]
+    for k, (w, b) in enumerate(par):
+        h = C.conv3d(h, w, b)
+        if k < len(par) - 1:
+            h = C.bf16_round(np.maximum(h, 0.0))
+        acts.append(h)
+    return h[0], acts
+
+
+def ref_backward_bf16(par, acts, gs):
+    """The oracle's backward with the GPU's BF16 storage of the loss gradient
+    and of every back-propagated (ReLU-masked) gradient."""
+    g = C.bf16_round(gs)[None]
+    grads = [None] * len(par)
+    for k in range(len(par) - 1, -1, -1):
+        gx, gw, gb = C.conv3d_backward(acts[k], par[k][0], g)
+        grads[k] = (gw, gb)
+        if k > 0:
+            g = C.bf16_round(gx * (acts[k] > 0.0))
+    return grads
+
+
+def rel2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+# several 128-cell MMA tiles with a ragged last tile, a grid smaller than one
+# tile, a long-row grid (three staged stages), and the training shape
 GRIDS = [(37, 9, 5), (5, 3, 2), (64, 4, 2)]
 
 
-@pytest.mark.parametrize("grid", GRIDS)
+@pytest.mark.parametrize("grid", GRIDS + [(64, 64, 64)])
 def test_forward_matches_oracle(grid):
     net = net_with_biases(1)
     n = int(np.prod(grid))
-    batch = 2
+    batch = 2 if n < 100000 else 1
     kap = np.concatenate([I.random_small(grid, 40 + k, contrast_exp=3, per_cell=True)["kappa"]
                           for k in range(batch)])
     t = host(net.forward(grid, dev(kap), batch=batch))
     par = oracle_params(net)
     for k in range(batch):
-        s_ref, _ = C.forward(par, C.features(kap[k * n:(k + 1) * n], grid))
+        x0 = C.features(kap[k * n:(k + 1) * n], grid)
+        s_ref, _ = ref_forward_bf16(par, x0)
         s = np.log(t[k * n:(k + 1) * n]).reshape(s_ref.shape)
-        assert np.max(np.abs(s - s_ref)) <= 1e-5 * max(1.0, np.max(np.abs(s_ref)))
+        scale = max(1.0, np.max(np.abs(s_ref)))
+        assert np.max(np.abs(s - s_ref)) <= 2e-3 * scale
+        assert rel2(s, s_ref) <= 1e-3
+        s64, _ = C.forward(par, x0)
+        assert rel2(s, s64) <= 1e-2
 
 
 @pytest.mark.parametrize("grid", GRIDS[:2])
@@ -106,23 +160,55 @@ def test_gradient_matches_oracle(grid):
     g = host(g).astype(np.float64)
     par = oracle_params(net)
     # the oracle's loss is a mean over one instance; over the batch it is the mean of the means
-    total = [np.zeros_like(w) for w, _ in par], [np.zeros_like(b) for _, b in par]
+    tot = {key: ([np.zeros_like(w) for w, _ in par], [np.zeros_like(b) for _, b in par])
+           for key in ("bf16", "fp64", "abs")}
     lsum = 0.0
     for k in range(batch):
         x0 = C.features(kap[k * n:(k + 1) * n], grid)
-        s, acts = C.forward(par, x0)
-        lk, gs = C.loss_and_grad(s, st[k * n:(k + 1) * n].astype(np.float64).reshape(s.shape))
-        grads = C.backward(par, acts, gs / batch)
+        stk = st[k * n:(k + 1) * n].astype(np.float64)
+        s, acts = ref_forward_bf16(par, x0)
+        lk, gs = C.loss_and_grad(s, stk.reshape(s.shape))
         lsum += lk / batch
-        for i, (gw, gb) in enumerate(grads):
-            total[0][i] += gw
-            total[1][i] += gb
-    ref = flat_grads(list(zip(total[0], total[1])))
-    assert abs(loss - lsum) <= 1e-6 * lsum
-    for w0, b0, cin, cout in OFF:
-        for lo, hi in ((w0, w0 + cout * cin * 27), (b0, b0 + cout)):
-            err = np.linalg.norm(g[lo:hi] - ref[lo:hi]) / max(np.linalg.norm(ref[lo:hi]), 1e-30)
-            assert err <= 1e-4, (w0, lo, err)
+        acts64, gs64 = _fwd64(par, x0, stk, batch)
+        for key, grads in (("bf16", ref_backward_bf16(par, acts, gs / batch)),
+                           ("fp64", C.backward(par, acts64, gs64)),
+                           ("abs", abs_terms(par, acts64, gs64))):
+            for i, (gw, gb) in enumerate(grads):
+                tot[key][0][i] += gw
+                tot[key][1][i] += gb
+    assert abs(loss - lsum) <= 1e-4 * lsum
+    mag = flat_grads(list(zip(*tot["abs"])))
+    for key, tol in (("bf16", 2e-3), ("fp64", 2e-2)) if n >= 1000 else (("bf16", 2e-3),):
+        ref = flat_grads(list(zip(*tot[key])))
+        for w0, b0, cin, cout in OFF:
+            for lo, hi in ((w0, w0 + cout * cin * 27), (b0, b0 + cout)):
+                if key == "bf16":
+                    err = rel2(g[lo:hi], ref[lo:hi])
+                else:
+                    err = float(np.linalg.norm(g[lo:hi] - ref[lo:hi]) / np.linalg.norm(mag[lo:hi]))
+                assert err <= tol, (key, w0, lo, err)
+
+
+def abs_terms(par, acts, gs):
+    """Per parameter, the sum over cells of the magnitudes of the terms of its
+    gradient, sum_q |gz_q| |x_q+off| (weights) and sum_q |gz_q| (biases), with
+    the FP64 oracle's back-propagated gz."""
+    g = gs[None]
+    out = [None] * len(par)
+    for k in range(len(par) - 1, -1, -1):
+        _, gw, gb = C.conv3d_backward(np.abs(acts[k]), par[k][0], np.abs(g))
+        out[k] = (gw, gb)
+        if k > 0:
+            gx, _, _ = C.conv3d_backward(acts[k], par[k][0], g)
+            g = gx * (acts[k] > 0.0)
+    return out
+
+
+def _fwd64(par, x0, stk, batch):
+    """(acts, gs / batch) of the plain FP64 oracle for one instance of the batch."""
+    s, acts = C.forward(par, x0)
+    _, gs = C.loss_and_grad(s, stk.reshape(s.shape))
+    return acts, gs / batch
 
 
 def test_adam_matches_oracle():
