@@ -183,6 +183,10 @@ def train(net, grid, kappas, targets, epochs=4, batch=8, lr=1e-3, seed=0, log=No
 
 
 WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__file__), "learned_filter_weights.txt")
+# The same network trained on the floor-0.01 target, for plain B_NTD (where the
+# rowsum filter leaves cond(B^{-1}A) near 1e5 on 64^3 GRF instances of contrast 1e4)
+WEIGHTS_NTD = __import__("os").path.join(__import__("os").path.dirname(__file__),
+                                         "learned_filter_weights_ntd.txt")
 
 
 def save_weights(net, path):
@@ -274,6 +278,8 @@ def _main(argv=None):
     tr.add_argument("--out", default=WEIGHTS)
     tr.add_argument("--log", default=None)
     tr.add_argument("--max-target-seconds", type=float, default=None)
+    tr.add_argument("--floor", type=float, default=FLOOR,
+                    help="target floor relative to max t* (0.1 suits B_c, 0.01 plain B_NTD)")
     ev = sub.add_parser("eval")
     ev.add_argument("--weights", default=WEIGHTS)
     ev.add_argument("--n", type=int, default=64)
@@ -298,7 +304,7 @@ def _main(argv=None):
     if a.cmd == "train":
         t0 = time.time()
         insts = I.workload_learned_train(count=a.count, n=a.n)
-        kappas, targets = make_targets(insts, max_seconds=a.max_target_seconds)
+        kappas, targets = make_targets(insts, floor=a.floor, max_seconds=a.max_target_seconds)
         t_targets = time.time() - t0
         print(f"targets: {len(kappas)} instances in {t_targets:.1f} s", flush=True)
         net = FilterNet(seed=0)
@@ -307,7 +313,7 @@ def _main(argv=None):
                      log=print)
         t_train = time.time() - t0
         save_weights(net, a.out)
-        rep = {"count": len(kappas), "requested": a.count, "n": a.n, "epochs": a.epochs,
+        rep = {"count": len(kappas), "requested": a.count, "n": a.n, "epochs": a.epochs, "floor": a.floor,
                "batch": a.batch, "lr": a.lr,
                "targets_s": t_targets, "train_s": t_train, "loss": hist}
         print(json.dumps(rep))
