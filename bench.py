@@ -302,7 +302,7 @@ def run_ours(args):
     ms, setup_ms, stats, clocks = timed_steps(step, kappa, b, x, args.steps, local)
     barrier()
     # ---- end to end through the public API with host buffers
-    e2e_steps = min(args.steps, args.e2e_steps)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))  # the line always carries an end-to-end number
     e2 = []
     barrier()
     torch.cuda.synchronize()
@@ -728,7 +728,7 @@ def main():
     ap.add_argument("--cpu-sample-iters", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed solves of the plain FP64 rowsum form beside the main arm (0: none)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps (at least 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -23,7 +23,7 @@ the paper; this module states them plainly:
   target       s* = log t* - mean(log t*), t* = sqrt(sum_k (theta_1/theta_k)
                y_k^2) over the 8 smallest Ritz pairs (theta_k, y_k) of B^{-1}A
                (y_k normalised to max |y_k| = 1), floored at `floor` * max t*
-               (the library trains with floor 0.1)
+               (the library trains with floor 0.01)
   Adam         Kingma & Ba (2015): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
                w -= lr * (m / (1-b1^k)) / (sqrt(v / (1-b2^k)) + eps)
   Lanczos      on B^{-1}A, which is self-adjoint in the A-inner product

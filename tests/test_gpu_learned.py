@@ -305,16 +305,16 @@ def test_trained_filter_gain_over_rowsum():
 
 
 def test_trained_ntd_filter_lowers_condition_estimate():
-    """The network trained on the floor-0.01 target (`learned train --floor 0.01`, 2000 64^3
+    """The committed network (trained on the floor-0.01 target by `learned train`, 2000 64^3
     GRF instances, seeds 10000-11999) against rowsum with plain B_NTD (Sec. II, FP32 factors,
     flexible CG) on held-out instances: the Lanczos estimate of cond(B^{-1}A) from the CG
     coefficients falls by more than 3x, and after the same 300 iterations the true residual is
     more than 100x smaller.  (Measured: estimates 7.7e3-1.6e4 against 9.1e4-1.2e5; the
     rowsum filter stays near 2e-2 after 600 iterations.)"""
     import os
-    if not os.path.exists(L.WEIGHTS_NTD):
+    if not os.path.exists(L.WEIGHTS):
         pytest.skip("no trained weights")
-    net = L.load_weights(L.WEIGHTS_NTD)
+    net = L.load_weights(L.WEIGHTS)
     for seed in (0, 1):
         w = I.workload_grf(seed=seed, n=64, exponent=2.0)
         kap, b = dev(w["kappa"]), dev(w["b"])
