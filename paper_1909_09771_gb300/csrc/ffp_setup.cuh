@@ -12,6 +12,10 @@
 //           half, saved for the twist plane.
 //   phase 1 (1 CTA): P_mz = Dhat_mz - (term from mz-1) - (term from mz+1), then
 //     its level-2 factorization.
+// The batched setup runs phase 0 fused in one launch per instance table.  The
+// single-instance setup runs every plane step of phase 0 as two launches, (a)-(b)
+// on the two CTAs of the chains and the cell-wise rest of (b)-(c) on the whole GPU
+// (setup_plane_kernel, setup_cells_kernel below), with the same arithmetic.
 // Level 2 (lines of P_i), twisted at my = floor((ny-1)/2), two warps per half
 // that split every line's slots (warps 0/2 and 1/3, see SlotSplit):
 //   T_0 = Dbar_0 / T_{ny-1} = Dbar_{ny-1}; T_k = Dbar_k - p X p with
@@ -21,6 +25,7 @@
 // Stored: l1 = x-band of T_k, minv = 1/M, l2 = y-band of P_i (l3 = z-band of A
 // is converted separately).
 #pragma once
+#include <algorithm>
 #include <cstring>
 
 #include "ffp_plane.cuh"
@@ -61,6 +66,44 @@ struct SetupPol {
     __device__ __forceinline__ double get_w(int k, int a) const { return V[(long)k * nx + a]; }
     __device__ __forceinline__ void put_out(int k, int a, double u) const { V[(long)k * nx + a] = u; }
 };
+
+// w = c3 (.) t of one cell of the next plane (t = 1 for rowsum).
+__device__ __forceinline__ double w_cell(const double *C, const double *T, long e) {
+    return __dmul_rn(C[e], T ? T[e] : 1.0);
+}
+// beta-hat = (B_P^{-1} w) ./ w of one cell (Sec. II-A), 1/P_ee where w vanishes.
+__device__ __forceinline__ double beta_cell(double v, double w, double pd) {
+    const bool z = fabs(w) < 1e-300;
+    return __ddiv_rn(z ? 1.0 : v, z ? pd : w);
+}
+// The Schur term C X C at cell e of the next plane dst (X = 2 beta - beta P beta,
+// or X = beta with `schur`), from beta-hat at e, e+1 and e+nx: written as the
+// term itself (to_mid: the twist plane collects both halves' terms) or as
+// P_dst = Dhat_dst - C X C.  The same rounded operations in every setup form.
+__device__ __forceinline__ void schur_cell(long e, int ix, int iy, int nx, int ny, int schur, double be,
+                                           double be1, double beny, const double *Pd, const double *Px,
+                                           const double *Py, const double *C, bool to_mid,
+                                           const double *dd, const double *dx, const double *dy,
+                                           double *od, double *ox, double *oy) {
+    const double xd = schur ? be : __fma_rn(2.0, be, -__dmul_rn(__dmul_rn(be, Pd[e]), be));
+    const double cd = __dmul_rn(__dmul_rn(C[e], xd), C[e]);
+    double cxo = 0.0, cyo = 0.0;
+    if (ix + 1 < nx && !schur) {
+        const double xo = __dmul_rn(__dmul_rn(-be, Px[e]), be1);
+        cxo = __dmul_rn(__dmul_rn(C[e], xo), C[e + 1]);
+    }
+    if (iy + 1 < ny && !schur) {
+        const double xo = __dmul_rn(__dmul_rn(-be, Py[e]), beny);
+        cyo = __dmul_rn(__dmul_rn(C[e], xo), C[e + nx]);
+    }
+    if (to_mid) {
+        od[e] = cd; ox[e] = cxo; oy[e] = cyo;
+    } else {
+        od[e] = __dsub_rn(dd[e], cd);
+        ox[e] = __dsub_rn(dx[e], cxo);
+        oy[e] = __dsub_rn(dy[e], cyo);
+    }
+}
 
 // State of the previous line T_prev as seen by this lane (this part's slots).
 template <int S>
@@ -435,7 +478,7 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
             const int ic = (i < dst) ? i : dst;
             const double *C = A.cz + ic * nxy;
             for (long e = tid; e < nxy; e += blockDim.x)
-                W[e] = C[e] * (A.t ? A.t[dst * nxy + e] : 1.0);
+                W[e] = w_cell(C, A.t ? A.t + dst * nxy : nullptr, e);
             __syncthreads();
             FFP_SPROF(const unsigned long long s2 = setup_stamp();)
             if (wid < 4) {
@@ -445,38 +488,19 @@ __device__ __forceinline__ void setup_body(const SetupArgs &A, int phase) {
             }
             __syncthreads();
             FFP_SPROF(const unsigned long long s3 = setup_stamp();)
-            for (long e = tid; e < nxy; e += blockDim.x) {
-                const bool z = fabs(W[e]) < 1e-300;  // one divide either way
-                V[e] = (z ? 1.0 : V[e]) / (z ? Pd[e] : W[e]);
-            }
+            for (long e = tid; e < nxy; e += blockDim.x) V[e] = beta_cell(V[e], W[e], Pd[e]);
             __syncthreads();
             FFP_SPROF(const unsigned long long s4 = setup_stamp();)
             const bool to_mid = (dst == mz);
             double *od = to_mid ? A.ws.sC[h][0] : A.ws.sP[h][(t + 1) & 1][0];
             double *ox = to_mid ? A.ws.sC[h][1] : A.ws.sP[h][(t + 1) & 1][1];
             double *oy = to_mid ? A.ws.sC[h][2] : A.ws.sP[h][(t + 1) & 1][2];
+            const long g0 = (long)dst * nxy;
             for (long e = tid; e < nxy; e += blockDim.x) {
                 const int ix = (int)(e % nx), iy = (int)(e / nx);
-                const double be = V[e];
-                const double xd = A.schur ? be : 2.0 * be - be * Pd[e] * be;
-                const double cd = C[e] * xd * C[e];
-                double cxo = 0.0, cyo = 0.0;
-                if (ix + 1 < nx && !A.schur) {
-                    const double xo = -be * Px[e] * V[e + 1];
-                    cxo = C[e] * xo * C[e + 1];
-                }
-                if (iy + 1 < ny && !A.schur) {
-                    const double xo = -be * Py[e] * V[e + nx];
-                    cyo = C[e] * xo * C[e + nx];
-                }
-                if (to_mid) {
-                    od[e] = cd; ox[e] = cxo; oy[e] = cyo;
-                } else {
-                    const long g = (long)dst * nxy + e;
-                    od[e] = A.d[g] - cd;
-                    ox[e] = A.cx[g] - cxo;
-                    oy[e] = A.cy[g] - cyo;
-                }
+                schur_cell(e, ix, iy, nx, ny, A.schur, V[e], ix + 1 < nx ? V[e + 1] : 0.0,
+                           iy + 1 < ny ? V[e + nx] : 0.0, Pd, Px, Py, C, to_mid, A.d + g0, A.cx + g0,
+                           A.cy + g0, od, ox, oy);
             }
             __syncthreads();
             FFP_SPROF(if (sprof) { const unsigned long long s5 = setup_stamp();
@@ -517,6 +541,115 @@ __global__ void __launch_bounds__(256) setup_kernel(const __grid_constant__ Setu
     setup_body<S>(A, phase);
 }
 
+// ---------------------------------------------------------------- single instance, per plane
+// The single-instance setup runs every level-3 plane step as two launches: the
+// level-2 factorization and the nested plane solve on one CTA per half (the two
+// chains), then the step's cell-wise work -- beta-hat, the next plane's Schur
+// term, that plane's l2 records -- spread over the whole GPU.  The arithmetic is
+// the fused form's, cell for cell (w_cell, beta_cell, schur_cell); beta-hat of
+// the neighbours e+1 and e+nx is recomputed where it is read, so the second
+// launch needs no grid-wide barrier, and w is formed where it is read.
+
+struct SetupPolOtf {  // the plane solve's right-hand side w = c3 (.) t, formed on read
+    const double *C, *T;
+    double *V;
+    int nx;
+    __device__ __forceinline__ double rhs(int k, int a) const { return w_cell(C, T, (long)k * nx + a); }
+    __device__ __forceinline__ void put_w(int k, int a, double w) const { V[(long)k * nx + a] = w; }
+    __device__ __forceinline__ double get_w(int k, int a) const { return V[(long)k * nx + a]; }
+    __device__ __forceinline__ void put_out(int k, int a, double u) const { V[(long)k * nx + a] = u; }
+};
+
+// Plane step t of level-3 half h: the plane i, its operator bands, the plane dst
+// the step eliminates towards and the z-coupling plane ic between them.
+struct PlaneStep {
+    int i, dst, ic, nl3;
+    bool to_mid;
+    const double *Pd, *Px, *Py;
+};
+__device__ __forceinline__ PlaneStep plane_step(const SetupArgs &A, int h, int t) {
+    const long nxy = (long)A.nx * A.ny;
+    const int mz = (A.nz - 1) / 2;
+    PlaneStep p;
+    p.nl3 = (h == 0) ? mz : A.nz - 1 - mz;
+    p.i = (h == 0) ? t : A.nz - 1 - t;
+    if (t == 0) {
+        p.Pd = A.d + p.i * nxy; p.Px = A.cx + p.i * nxy; p.Py = A.cy + p.i * nxy;
+    } else {
+        p.Pd = A.ws.sP[h][t & 1][0]; p.Px = A.ws.sP[h][t & 1][1]; p.Py = A.ws.sP[h][t & 1][2];
+    }
+    p.dst = (t == p.nl3 - 1) ? mz : ((h == 0) ? p.i + 1 : p.i - 1);
+    p.ic = (p.i < p.dst) ? p.i : p.dst;
+    p.to_mid = (p.dst == mz);
+    return p;
+}
+
+// Launch 1 of plane step t: one CTA per half (blockIdx.x), 256 threads.
+template <int S>
+__global__ void __launch_bounds__(256) setup_plane_kernel(const __grid_constant__ SetupArgs A, int t) {
+    extern __shared__ __align__(16) double sm[];
+    const int h = blockIdx.x;
+    const PlaneStep p = plane_step(A, h, t);
+    if (A.nz <= 1 || t >= p.nl3) return;
+    const int nx = A.nx, ny = A.ny;
+    const long nxy = (long)nx * ny;
+    double *gbuf = sm, *lbuf = sm + 4 * nx, *meet = sm + 10 * nx, *ex = sm + 14 * nx;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, half = wid & 1;
+    SlotSplit sp = make_split<S>(wid >> 1, ex + half * 512, 3 + half);
+    const LineMap L(nx);
+    const int cnt = lane_count<S>(L, lane);
+    FFP_SPROF(const bool sprof = h == 0 && tid == 0; const unsigned long long s0 = setup_stamp();)
+    if (t == 0)  // the first plane's l2 records (later planes': launch 2 of the step before)
+        for (long e = tid; e < nxy; e += blockDim.x)
+            put_factor(A.rec, ((long)p.i * ny + e / nx) * rec_len(S) +
+                                  rec_cell(nx, S, REC_L2, MID_L2, (int)(e % nx)),
+                       p.Py[e], A.prec);
+    double *l1d = A.ws.sF[h][0], *mid = A.ws.sF[h][1];
+    if (wid < 4)
+        level2_setup<S>(L, nx, ny, p.Pd, p.Px, p.Py, A.t ? A.t + p.i * nxy : nullptr, l1d, mid, A.rec,
+                        A.l1n, (long)p.i * ny, A.prec, lbuf, meet, half, lane, cnt, A.ws.flags, sp,
+                        A.schur FFP_SPROF(, nullptr));
+    __syncthreads();
+    FFP_SPROF(const unsigned long long s1 = setup_stamp();)
+    if (wid < 4) {
+        SetupPolOtf pol{A.cz + p.ic * nxy, A.t ? A.t + p.dst * nxy : nullptr, A.ws.sW[h][1], nx};
+        plane_solve<S, false, double, double>(L, nx, ny, l1d, mid, p.Py, pol, gbuf, half, lane, cnt, sp);
+    }
+    FFP_SPROF(if (sprof) {
+        const unsigned long long s2 = setup_stamp();
+        atomicAdd(&g_setup_prof[0], s1 - s0);
+        atomicAdd(&g_setup_prof[2], s2 - s1);
+        atomicAdd(&g_setup_prof[8], 1ull);
+    })
+}
+
+// Launch 2 of plane step t: the cell-wise work, blockIdx.y = half.
+template <int S>
+__global__ void __launch_bounds__(256) setup_cells_kernel(const __grid_constant__ SetupArgs A, int t) {
+    const int h = blockIdx.y;
+    const PlaneStep p = plane_step(A, h, t);
+    if (A.nz <= 1 || t >= p.nl3) return;
+    const int nx = A.nx, ny = A.ny;
+    const long nxy = (long)nx * ny;
+    const double *C = A.cz + p.ic * nxy, *T = A.t ? A.t + p.dst * nxy : nullptr;
+    const double *V = A.ws.sW[h][1];
+    double *od = p.to_mid ? A.ws.sC[h][0] : A.ws.sP[h][(t + 1) & 1][0];
+    double *ox = p.to_mid ? A.ws.sC[h][1] : A.ws.sP[h][(t + 1) & 1][1];
+    double *oy = p.to_mid ? A.ws.sC[h][2] : A.ws.sP[h][(t + 1) & 1][2];
+    const long g0 = (long)p.dst * nxy;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nxy; e += (long)gridDim.x * blockDim.x) {
+        const int ix = (int)(e % nx), iy = (int)(e / nx);
+        const double be = beta_cell(V[e], w_cell(C, T, e), p.Pd[e]);
+        const double be1 = ix + 1 < nx ? beta_cell(V[e + 1], w_cell(C, T, e + 1), p.Pd[e + 1]) : 0.0;
+        const double beny = iy + 1 < ny ? beta_cell(V[e + nx], w_cell(C, T, e + nx), p.Pd[e + nx]) : 0.0;
+        schur_cell(e, ix, iy, nx, ny, A.schur, be, be1, beny, p.Pd, p.Px, p.Py, C, p.to_mid, A.d + g0,
+                   A.cx + g0, A.cy + g0, od, ox, oy);
+        if (!p.to_mid)  // the next plane's l2 records (the twist plane's: phase 1)
+            put_factor(A.rec, ((long)p.dst * ny + iy) * rec_len(S) + rec_cell(nx, S, REC_L2, MID_L2, ix),
+                       oy[e], A.prec);
+    }
+}
+
 #ifdef FFP_STEP_PROFILE
 inline cudaError_t setup_profile_read(unsigned long long *host) {
     return cudaMemcpyFromSymbol(host, g_setup_prof, sizeof(g_setup_prof));
@@ -536,6 +669,7 @@ cudaError_t setup_table_for_slots(const SetupArgs *table, int count, int nx_max,
     return cudaGetLastError();
 }
 
+// Single instance: two launches per level-3 plane step (see above), then the twist plane.
 template <int S>
 cudaError_t setup_for_slots(const KernelCtx &c, const double *t, cudaStream_t st) {
     SetupArgs a;
@@ -543,8 +677,24 @@ cudaError_t setup_for_slots(const KernelCtx &c, const double *t, cudaStream_t st
     const size_t smem = sizeof(double) * (14 * (size_t)a.nx + 1024);
     cudaError_t e = cudaFuncSetAttribute(setup_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(setup_plane_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (a.nz > 1) setup_kernel<S><<<2, 256, smem, st>>>(a, nullptr, 0);
+#ifdef FFP_STEP_PROFILE
+    {
+        void *prof = nullptr;
+        if (cudaGetSymbolAddress(&prof, g_setup_prof) == cudaSuccess)
+            cudaMemsetAsync(prof, 0, sizeof(g_setup_prof), st);
+    }
+#endif
+    const int mz = (a.nz - 1) / 2;
+    const int steps = (a.nz > 1) ? (mz > a.nz - 1 - mz ? mz : a.nz - 1 - mz) : 0;
+    const long nxy = (long)a.nx * a.ny;
+    const int cell_blocks = (int)std::min<long>((nxy + 255) / 256, 304);
+    for (int s = 0; s < steps; ++s) {
+        setup_plane_kernel<S><<<2, 256, smem, st>>>(a, s);
+        setup_cells_kernel<S><<<dim3(cell_blocks, 2), 256, 0, st>>>(a, s);
+    }
     setup_kernel<S><<<1, 256, smem, st>>>(a, nullptr, 1);
     return cudaGetLastError();
 }
