@@ -598,7 +598,8 @@ __global__ void __launch_bounds__(256) setup_plane_kernel(const __grid_constant_
     SlotSplit sp = make_split<S>(wid >> 1, ex + half * 512, 3 + half);
     const LineMap L(nx);
     const int cnt = lane_count<S>(L, lane);
-    FFP_SPROF(const bool sprof = h == 0 && tid == 0; const unsigned long long s0 = setup_stamp();)
+    FFP_SPROF(const bool sprof = h == 0 && tid == 0; unsigned long long lacc[16] = {0};
+              const unsigned long long s0 = setup_stamp();)
     if (t == 0)  // the first plane's l2 records (later planes': launch 2 of the step before)
         for (long e = tid; e < nxy; e += blockDim.x)
             put_factor(A.rec, ((long)p.i * ny + e / nx) * rec_len(S) +
@@ -608,7 +609,7 @@ __global__ void __launch_bounds__(256) setup_plane_kernel(const __grid_constant_
     if (wid < 4)
         level2_setup<S>(L, nx, ny, p.Pd, p.Px, p.Py, A.t ? A.t + p.i * nxy : nullptr, l1d, mid, A.rec,
                         A.l1n, (long)p.i * ny, A.prec, lbuf, meet, half, lane, cnt, A.ws.flags, sp,
-                        A.schur FFP_SPROF(, nullptr));
+                        A.schur FFP_SPROF(, sprof ? lacc : nullptr));
     __syncthreads();
     FFP_SPROF(const unsigned long long s1 = setup_stamp();)
     if (wid < 4) {
@@ -619,6 +620,7 @@ __global__ void __launch_bounds__(256) setup_plane_kernel(const __grid_constant_
         const unsigned long long s2 = setup_stamp();
         atomicAdd(&g_setup_prof[0], s1 - s0);
         atomicAdd(&g_setup_prof[2], s2 - s1);
+        for (int q = 5; q < 8; ++q) atomicAdd(&g_setup_prof[q], lacc[q]);
         atomicAdd(&g_setup_prof[8], 1ull);
     })
 }

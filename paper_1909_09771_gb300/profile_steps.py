@@ -2,11 +2,12 @@
 build of the library (python -m paper_1909_09771_gb300.build --profile, which
 writes libffp_profile.so beside libffp.so; the normal library has no stamps).
 
-It also reports the setup's per-plane phases (slot counts 8 and 11, so
-nx from 130 to 353): the level-2 factorization of the plane (line Schur terms,
-line pivots, line stores), the w vector, the nested plane solve for beta-hat,
-beta = v ./ w, and the Schur term of the next plane, per plane of the first
-level-3 half.
+It also reports the setup (slot counts 8 and 11, so nx from 130 to 353): its
+time (CUDA events), and per plane step of the first level-3 half the chain
+CTA's phases, the level-2 factorization of the plane (line Schur terms, line
+pivots, line stores) and the nested plane solve for beta-hat; the cell-wise
+phases (beta-hat, the next plane's Schur term) run as a separate launch over
+the whole GPU.
 
 The profiling build stamps clock64 around the segments of every line step of
 one compute warp (level-2 half 0 of the first level-3 half, phase 0 launch)
@@ -32,7 +33,14 @@ from paper_1909_09771_gb300 import inputs as I
 
 def budget(n, lib):
     w = I.workload_grf(seed=0, n=n)
-    P = ffp.Preconditioner(w["grid"], torch.as_tensor(w["kappa"], device="cuda"), w["bc"], "fp32")
+    kap = torch.as_tensor(w["kappa"], device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    P = ffp.Preconditioner(w["grid"], kap, w["bc"], "fp32")
+    e1.record()
+    torch.cuda.synchronize()
+    setup_ms = e0.elapsed_time(e1)
     _, st = P.solve(torch.as_tensor(w["b"], device="cuda"), rtol=1e-30, maxit=5, check=False)
     torch.cuda.synchronize()
     prof = (ctypes.c_ulonglong * 16)()
@@ -44,9 +52,10 @@ def budget(n, lib):
     if lib.ffp_setup_profile(ctypes.cast(sprof, ctypes.c_void_p)) == 0 and sprof[8] > 0:
         q = list(sprof)
         npl = q[8]
+        # the chain CTAs' phases per plane step; the cell-wise phases run as a separate
+        # launch over the whole GPU and are in setup_ms only
         setup = {"planes": npl, "level2": q[0] / npl, "line_schur": q[5] / npl, "line_pivots": q[6] / npl,
-                 "line_store": q[7] / npl, "w": q[1] / npl, "plane_solve": q[2] / npl, "beta": q[3] / npl,
-                 "next_schur": q[4] / npl, "loop": q[9] / npl}
+                 "line_store": q[7] / npl, "plane_solve": q[2] / npl, "setup_ms": setup_ms}
     depth = (w["grid"][2] + 1) * (w["grid"][1] + 1)
     ms = st["ntd_ms"] / max(st["napply"], 1)
     nl, nu = max(p[4], 1), max(p[9], 1)
@@ -83,10 +92,10 @@ def main(argv):
               f"try failed: {r['first_try_misses']}")
         q = r["setup"]
         if q:
-            print(f"  setup, cycles per plane ({q['planes']} planes of one level-3 half): level-2 "
-                  f"{q['level2']:.0f} (line Schur {q['line_schur']:.0f}, pivots {q['line_pivots']:.0f}, "
-                  f"stores {q['line_store']:.0f}), w {q['w']:.0f}, plane solve {q['plane_solve']:.0f}, "
-                  f"beta {q['beta']:.0f}, next Schur {q['next_schur']:.0f}, loop {q['loop']:.0f}")
+            print(f"  setup {q['setup_ms']:.0f} ms (profiling build, CUDA events); chain-CTA cycles per "
+                  f"plane step ({q['planes']} steps of one level-3 half): level-2 {q['level2']:.0f} (line "
+                  f"Schur {q['line_schur']:.0f}, pivots {q['line_pivots']:.0f}, stores {q['line_store']:.0f}), "
+                  f"plane solve {q['plane_solve']:.0f}")
 
 
 if __name__ == "__main__":
